@@ -1,0 +1,15 @@
+"""The oracle: plain, slow, obviously correct CPU evaluations of the Harris pattern pipeline.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import, call, link or run anything in this package. The CUDA library and its
+Python binding never do, and this package never imports them: the two share no code.
+
+* ``patterns``  -- the data-parallel patterns (map, zip, reduce, split, join, slide, slide2D,
+                   pad_clamp, transpose, iterate) and their adjoints, on nested lists in FP64.
+* ``harris``    -- the Harris pipeline as a composition of those patterns, and its reference
+                   gradient by reverse mode through the pattern adjoints.
+* ``cref``      -- the same pipeline as FP64 C loops, stage by stage (``harris_ref.c``), with
+                   point-sampled forms for images too large for full FP64 stage arrays.
+* ``mv``        -- the paper's running example (matrix-vector multiply) in both its high-level
+                   and its optimised pattern form.
+"""
