@@ -1,0 +1,342 @@
+"""Benchmark of the fused Harris pipeline on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--size S]
+
+One step is the whole hot path over one batch: the fused forward kernel (gray -> Sobel ->
+products -> box sum -> response, R written once) and the fused adjoint kernel (+ the fixed-order
+parameter reduction) over the 8192 x 8192 x 3 float32 salt-noise image (uniform [0,1) with 5%
+of pixels set to 1.0, CLAMP borders, kappa 0.04) with an N(0,1) cotangent (seed 1). Inputs are
+synthetic, drawn on the host with the torch CPU generator, and larger than L2, so no flush is
+needed between steps. Rank 0 prints one JSON line.
+
+--impl reference times the oracle (the FP64 C reference of oracle/, on the host cores) on a
+bounded band of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+ALG_BYTES_PER_PX = {  # unique HBM bytes per output pixel (image in + map out, etc.)
+    ("fwd", 4): 16, ("bwd", 4): 28, ("fwd", 2): 8, ("bwd", 2): 14, ("fused", 4): 32, ("fused", 2): 16,
+}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2201_03611_b300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str) -> float | None:
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was taken on the
+    current kernel sources (a line 'traffic_bytes_per_launch: <kernel> <workload> <bytes> <hash>')."""
+    want = kernel_source_hash()
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(p):
+            m = re.match(r"\s*traffic_bytes_per_launch:\s+(\S+)\s+(\S+)\s+([0-9.eE+]+)\s+(\w+)", line)
+            if m and m.group(1) == kernel and m.group(2) == workload and m.group(4) == want:
+                return float(m.group(3))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict | None:
+        if self.proc is None or not self.path:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        # samples under load only: the sampler also sees the idle edges of the region
+        loaded = [v for v in sm if v >= 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _barrier_sync(world):
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+
+def _max_over_ranks(v: float, world: int, device) -> float:
+    if world == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: int) -> dict:
+    """The FP64 C oracle (as it stands) on a band of the workload: forward + reverse pass."""
+    from oracle import cref
+    wx, wy = wl.sobel_weights()
+    band = img[:rows].contiguous()
+    gb = g[:rows].contiguous()
+    cref.lib()
+    t0 = time.perf_counter()
+    cref.forward(band, kappa, wx, wy, "clamp")
+    cref.backward(band, gb, kappa, wx, wy, "clamp")
+    dt = time.perf_counter() - t0
+    px = band.shape[0] * band.shape[1]
+    return {"value": px / dt / 1e9, "unit": "Gpixel/s", "cores": cref.num_threads(), "kind": "oracle",
+            "sample": f"FP64 C oracle, forward + reverse pass over rows 0..{rows - 1} of the "
+                      f"{img.shape[0]}x{img.shape[1]} image as a CLAMP image ({px} px, {dt:.2f} s)"}
+
+
+def run_ours(args, world, rank, local) -> dict | None:
+    import paper_2201_03611_b300 as S
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    size = args.size
+    img_h = wl.salt_image(size, size) if size != 8192 else wl.salt_8192()["img"]
+    g_h = wl.random_cotangent(size, size, seed=1)
+    kappa = wl.KAPPA
+    wx, wy = wl.sobel_weights()
+    img = img_h.to(device)
+    g = g_h.to(device)
+    k = torch.tensor([kappa], device=device)
+    dwx, dwy = wx.to(device), wy.to(device)
+    out = torch.empty(size, size, device=device)
+    gimg = torch.empty_like(img)
+    gk = torch.empty(1, device=device)
+    gwx = torch.empty(3, 3, device=device)
+    gwy = torch.empty(3, 3, device=device)
+    ws = torch.empty(S.bwd_workspace_bytes(size, size, "clamp"), dtype=torch.uint8, device=device)
+
+    def step():
+        S.pipeline_fwd(img, k, dwx, dwy, "clamp", out=out)
+        S.pipeline_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, grad_img=gimg)
+
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    stream = torch.cuda.current_stream(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(device.index if device.index is not None else 0) as clk:
+        _barrier_sync(world)
+        t0.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            S.pipeline_fwd(img, k, dwx, dwy, "clamp", out=out)
+            ev[i][1].record(stream)
+            S.pipeline_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, grad_img=gimg)
+            ev[i][2].record(stream)
+        t1.record(stream)
+        _barrier_sync(world)
+    total_ms = _max_over_ranks(t0.elapsed_time(t1), world, device)
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    px = size * size
+    value = world * px * K / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: pinned host -> device, both passes,
+    # device -> host of R, d img and the parameter cotangents, every step
+    img_pin = img_h.pin_memory()
+    g_pin = g_h.pin_memory()
+    out_pin = torch.empty(size, size).pin_memory()
+    gimg_pin = torch.empty(size, size, 3).pin_memory()
+    par_pin = torch.empty(19).pin_memory()
+    e2e_steps = max(2, min(10, K))
+
+    def e2e_step():
+        img.copy_(img_pin, non_blocking=True)
+        g.copy_(g_pin, non_blocking=True)
+        S.pipeline_fwd(img, k, dwx, dwy, "clamp", out=out)
+        _, pk, pwx, pwy = S.pipeline_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, grad_img=gimg)
+        out_pin.copy_(out, non_blocking=True)
+        gimg_pin.copy_(gimg, non_blocking=True)
+        par_pin[0:1].copy_(pk, non_blocking=True)
+        par_pin[1:10].copy_(pwx.reshape(9), non_blocking=True)
+        par_pin[10:19].copy_(pwy.reshape(9), non_blocking=True)
+    e2e_step()
+    _barrier_sync(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    _barrier_sync(world)
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world, device) / e2e_steps
+    h2d = img_h.numel() * 4 + g_h.numel() * 4
+    d2h = out.numel() * 4 + gimg.numel() * 4 + 19 * 4
+
+    if rank != 0:
+        return None
+    peak, peak_kind = _peaks()
+    kern = {}
+    for name, ms, kname in (("fwd", fwd_ms, "harris_fwd_kernel"), ("bwd", bwd_ms, "harris_bwd_kernel")):
+        alg = ALG_BYTES_PER_PX[(name, 4)] * px
+        kern[name] = {"kernel": kname, "ms": ms, "gpix_s": px / (ms * 1e-3) / 1e9,
+                      "algorithmic_bytes": alg, "gb_s": alg / (ms * 1e-3) / 1e9,
+                      "frac_of_measured_hbm": alg / (ms * 1e-3) / 1e9 / peak}
+    dom = max(kern, key=lambda n: kern[n]["ms"])
+    wname = f"salt_{size}"
+    traffic = ncu_traffic(kern[dom]["kernel"], wname)
+    line = {
+        "metric": "Gpixel/s fwd & fwd+bwd, % of HBM peak; bf16 vs fp32 at stated error",
+        "value": value, "unit": "Gpixel/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wname}: {size}x{size}x3 f32 HWC, uniform [0,1) + 5% salt (seed 0), CLAMP, "
+                               f"kappa 0.04, default Sobel; step = fused forward + fused adjoint with an "
+                               f"N(0,1) cotangent (seed 1)",
+                   "pixels_per_step": px, "l2": "inputs (image and cotangent) exceed the 126 MB L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": kern[dom]["kernel"], "achieved": kern[dom]["gb_s"], "peak": peak,
+                     "unit": "GB/s", "frac": kern[dom]["gb_s"] / peak, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": kern[dom]["algorithmic_bytes"]},
+        "kernels": kern,
+        "fwd_gpix_s": kern["fwd"]["gpix_s"],
+        "e2e": {"value": px / (e2e_ms * 1e-3) / 1e9 * world, "unit": "Gpixel/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * K,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(img_h, g_h, kappa, rows=args.cpu_rows)
+    return line
+
+
+def run_reference(args, world, rank) -> dict | None:
+    """The oracle as the reference arm: FP64 C reference on the host cores, bounded band."""
+    if rank != 0:
+        return None
+    size = args.size
+    img_h = wl.salt_image(size, size) if size != 8192 else wl.salt_8192()["img"]
+    g_h = wl.random_cotangent(size, size, seed=1)
+    rows = args.cpu_rows
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_sample(img_h, g_h, wl.KAPPA, rows=min(rows, 64))
+    vals = []
+    t0 = time.perf_counter()
+    sample = None
+    for _ in range(args.steps):
+        sample = cpu_oracle_sample(img_h, g_h, wl.KAPPA, rows=rows)
+        vals.append(sample["value"])
+        if time.perf_counter() - t0 > args.ref_budget_s:
+            break
+    value = statistics.median(vals)
+    px = rows * size
+    sample["value"] = value
+    return {"impl": "reference", "metric": "Gpixel/s fwd & fwd+bwd, % of HBM peak; bf16 vs fp32 at stated error",
+            "value": value, "unit": "Gpixel/s", "n_gpus": world, "steps": len(vals), "warmup": args.warmup,
+            "ms_per_step": px / value / 1e9 * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"salt_{size}: oracle forward + reverse pass on rows 0..{rows - 1}",
+                       "pixels_per_step": px},
+            "cpu_baseline": sample,
+            "e2e": {"value": value, "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--cpu-rows", type=int, default=2048)
+    ap.add_argument("--ref-budget-s", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        if world > 1:
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, world, rank, local)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

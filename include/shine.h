@@ -1,0 +1,188 @@
+/*
+ * shine.h -- C ABI of the fused Harris pattern pipeline on one GPU (sm_103a).
+ *
+ * The pipeline is a composition of data-parallel patterns applied to an RGB image:
+ *
+ *   A1  G  = map(grayscale)(img)                       gray = 0.299 r + 0.587 g + 0.114 b
+ *   A2  Ix = map(reduce(+) . zip(W_x))(slide2D(3,1)(pad(G)))      and Iy with W_y
+ *   A3  P  = map((ix, iy) -> (ix*ix, ix*iy, iy*iy))(zip(Ix, Iy))
+ *   A4  S  = map(reduce(+))(slide2D(3,1)(pad(P)))       unnormalised 3x3 box sum, per plane
+ *   A5  R  = map((sxx, sxy, syy) -> sxx*syy - sxy^2 - kappa*(sxx+syy)^2)(S)
+ *
+ * map, zip and reduce are the RISE primitives of the paper (Sec. 4.1); fusing the stages
+ * into one kernel with no intermediate buffer follows its map-fusion and fuseReduceMap
+ * rewrite rules (Sec. 4.2); only the result is written to global memory (toMem(Global),
+ * Sec. 5.3). slide2D(3,1) makes the 3x3 windows window[a][b] = x[i+a][j+b]; the weights are
+ * applied as a correlation (window[a][b] * W[a][b]); x is the column index.
+ *
+ * Borders.  SHINE_VALID: no padding; each 3x3 stage shrinks by 2, the output is (H-4) x (W-4)
+ * and needs H, W >= 5.  SHINE_CLAMP: pad_clamp2D(1) before each 3x3 stage (index clamp(i-1,
+ * 0, n-1)), so the output is H x W for any H, W >= 1. The products are clamped at their own
+ * stage, not recomputed from a further-clamped gray image.
+ *
+ * Layouts.  Images are H rows of W pixels, each pixel 3 interleaved channels (r, g, b),
+ * row-major, channel fastest; img_pitch is the distance between rows in ELEMENTS (>= 3W).
+ * Outputs and cotangents are H_out x W_out single-channel maps with their own pitch in
+ * elements (>= W_out). Weights wx, wy are 3x3 row-major float32 (wx[3a + b] = W_x[a][b]);
+ * kappa is one float32. All pointers are DEVICE pointers unless marked (host); every buffer
+ * is owned by the caller. Arithmetic is float32 whatever the storage type; the response
+ * step A5 is always float32.
+ *
+ * Fast-path alignment.  Rows are staged with 16-byte (float32) or 8-byte (bf16/fp16) copies
+ * when the image pointer and img_pitch * sizeof(element) are multiples of that size, and
+ * stored with 16- / 8-byte stores when the output pointer and pitch allow; otherwise the call
+ * takes an element-wise path that gives identical results, more slowly.
+ *
+ * Errors.  Argument errors are detected on the host and returned before anything is
+ * launched; launch failures come back as SHINE_ERR_CUDA (the CUDA error is then available
+ * from shine_last_cuda_error). Calls are asynchronous on the given stream, never
+ * synchronise, never allocate (except shine_plan_create), never throw, and are reentrant.
+ * Gradients are OVERWRITTEN, not accumulated; a NULL gradient pointer skips that output.
+ */
+#ifndef SHINE_H_
+#define SHINE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SHINE_API __attribute__((visibility("default")))
+#else
+#define SHINE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SHINE_OK = 0,
+    SHINE_ERR_INVALID_ARG = 1,  /* NULL pointer, bad enum, bad shape or pitch */
+    SHINE_ERR_ALIGNMENT = 2,    /* a pointer that must be 4-byte aligned is not */
+    SHINE_ERR_WORKSPACE = 3,    /* workspace missing or smaller than required */
+    SHINE_ERR_UNSUPPORTED = 4,  /* a combination this build does not implement */
+    SHINE_ERR_CUDA = 5          /* a CUDA call or kernel launch failed */
+} shine_status;
+
+typedef enum { SHINE_F32 = 0, SHINE_BF16 = 1, SHINE_F16 = 2 } shine_dtype;
+typedef enum { SHINE_VALID = 0, SHINE_CLAMP = 1 } shine_border;
+
+/* Output size of the pipeline for an H x W image (host helper; 0 on success). */
+SHINE_API shine_status shine_output_shape(int64_t H, int64_t W, shine_border border, int64_t* H_out,
+                                int64_t* W_out);
+
+/*
+ * Forward pass: R = A5(A4(A3(A2(A1(img))))) in one fused kernel (no intermediate in HBM).
+ *   img       [H][img_pitch] elements of type dt (3 channels per pixel)
+ *   kappa     [1] float32, wx/wy [9] float32 (device)
+ *   out       [H_out][out_pitch] elements of type out_dt
+ *   stream    a cudaStream_t (NULL = legacy default stream)
+ * Shapes: H, W >= 1 (CLAMP) or >= 5 (VALID); H, W <= 2^30; pitches >= 3W and >= W_out.
+ */
+SHINE_API shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t img_pitch,
+                                shine_dtype dt, shine_border border, const float* kappa,
+                                const float* wx, const float* wy, void* out, int64_t out_pitch,
+                                shine_dtype out_dt, void* stream);
+
+/*
+ * Forward and backward in one pass, for when the cotangent grad_out is known before R is
+ * needed (a loss sum(w * R) with fixed weights w): writes R (type dt, nullable) and the same
+ * cotangents as shine_pipeline_bwd. Reads the image and grad_out once and writes R and
+ * grad_img once; uses the workspace size of shine_pipeline_bwd_workspace.
+ */
+SHINE_API shine_status shine_pipeline_fwd_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch,
+                                    shine_dtype dt, shine_border border, const float* kappa,
+                                    const float* wx, const float* wy, const void* grad_out,
+                                    int64_t gout_pitch, void* out, int64_t out_pitch,
+                                    void* grad_img, int64_t gimg_pitch, float* grad_kappa,
+                                    float* grad_wx, float* grad_wy, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
+/* Workspace (bytes, host out-param) that shine_pipeline_bwd needs for an H x W image. */
+SHINE_API shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border border,
+                                          size_t* bytes);
+
+/*
+ * Backward pass (vector-Jacobian product) of L = sum(grad_out * R): reverse mode through the
+ * same patterns -- each stencil's adjoint is its transposed stencil (overlap-add), each clamp
+ * pad's adjoint folds the padded cotangent onto the clamped index, and the shared parameters'
+ * cotangents are sums over all pixels. The Sobel stage is recomputed, not read back.
+ *   grad_out   [H_out][gout_pitch] of type gout_dt (device)
+ *   grad_img   [H][gimg_pitch] of type dt, 3 channels per pixel (nullable)
+ *   grad_kappa [1], grad_wx [9], grad_wy [9] float32 (each nullable)
+ *   workspace  at least shine_pipeline_bwd_workspace() bytes of device memory, 16-byte
+ *              aligned; its contents are scratch (per-tile partial sums)
+ * The parameter cotangents are reduced in a fixed order in float64, so repeated calls give
+ * bit-identical results.
+ */
+SHINE_API shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch,
+                                shine_dtype dt, shine_border border, const float* kappa,
+                                const float* wx, const float* wy, const void* grad_out,
+                                int64_t gout_pitch, shine_dtype gout_dt, void* grad_img,
+                                int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
+                                float* grad_wy, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Many images of different sizes in one persistent launch.
+ *
+ * shine_plan_create builds, on the host and then once on the device, the tile list of a fixed
+ * set of image shapes (HW: host array of n (H, W) pairs), choosing the tile height per shape
+ * bucket (from tune_cache_path when given and it holds an entry for this GPU, else a built-in
+ * rule). mode: SHINE_MODE_FWD computes R only; SHINE_MODE_FWD_BWD also computes the
+ * cotangents of L = sum_i sum(grad_out_i * R_i) in the same pass (grad_out is an input given
+ * up front). This is the only call that allocates (host memory and one device buffer).
+ */
+typedef struct shine_plan shine_plan;
+enum { SHINE_MODE_FWD = 1, SHINE_MODE_FWD_BWD = 3 };
+
+typedef struct {
+    const void* img;       /* [H][img_pitch], 3 channels, plan dtype */
+    void* out;             /* [H_out][out_pitch], plan dtype (nullable in FWD_BWD mode) */
+    const void* grad_out;  /* [H_out][gout_pitch], plan dtype (FWD_BWD mode) */
+    void* grad_img;        /* [H][gimg_pitch], plan dtype (FWD_BWD mode, nullable) */
+    int64_t H, W;
+    int64_t img_pitch, out_pitch, gout_pitch, gimg_pitch;
+} shine_image_desc;
+
+SHINE_API shine_status shine_plan_create(const int64_t* HW, int32_t n, shine_dtype dt, shine_border border,
+                               int32_t mode, const char* tune_cache_path, shine_plan** plan);
+
+/* Device workspace (bytes) the batched call needs for this plan. */
+SHINE_API shine_status shine_plan_workspace(const shine_plan* plan, size_t* bytes);
+
+/* Tile height the plan chose for image i (host; for tests and reports). */
+SHINE_API shine_status shine_plan_tile_rows(const shine_plan* plan, int32_t i, int32_t* rows);
+
+/*
+ * Run the plan: descs is a DEVICE array of n image descriptors (same order and shapes as at
+ * plan creation), kappa [n] one per image, wx/wy [9] shared by every image. grad_kappa [n],
+ * grad_wx [9], grad_wy [9] are float32 outputs (nullable; FWD_BWD mode). Launches a
+ * persistent kernel (one CTA per SM slot, tiles claimed from an atomic counter in the
+ * workspace) and a fixed-order reduction; no allocation and no synchronisation, so the call
+ * can be captured in a CUDA graph. Results do not depend on which CTA ran which tile.
+ */
+SHINE_API shine_status shine_pipeline_batched(const shine_plan* plan, const shine_image_desc* descs,
+                                    const float* kappa, const float* wx, const float* wy,
+                                    float* grad_kappa, float* grad_wx, float* grad_wy,
+                                    void* workspace, size_t ws_bytes, void* stream);
+
+SHINE_API void shine_plan_destroy(shine_plan* plan);
+
+/*
+ * Key under which the tuning cache stores entries for the current device (host call): GPU
+ * name, compute capability, SM count and CUDA runtime version. Writes at most len bytes
+ * (NUL-terminated) to buf and returns the key's length, or -1 when no device is visible.
+ */
+SHINE_API int shine_tune_key(char* buf, size_t len);
+
+/* Static description of a status code. */
+SHINE_API const char* shine_status_string(shine_status s);
+
+/* The cudaError_t (as int) of the last SHINE_ERR_CUDA returned on this host thread. */
+SHINE_API int shine_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHINE_H_ */

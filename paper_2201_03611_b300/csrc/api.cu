@@ -1,0 +1,223 @@
+// extern "C" entry points of libshine (declared in include/shine.h): argument validation on
+// the host, the work decomposition, and the kernel launches. Nothing here allocates device
+// memory except shine_plan_create (in batched.cu), and nothing synchronises.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "harris_kernels.h"
+#include "shine.h"
+#include "shine_host.h"
+
+namespace shine {
+
+thread_local int g_last_cuda_error = 0;
+
+shine_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SHINE_OK;
+    g_last_cuda_error = (int)e;
+    return SHINE_ERR_CUDA;
+}
+
+size_t dtype_size(int dt) { return dt == SHINE_F32 ? 4 : 2; }
+bool dtype_ok(int dt) { return dt == SHINE_F32 || dt == SHINE_BF16 || dt == SHINE_F16; }
+bool border_ok(int b) { return b == SHINE_VALID || b == SHINE_CLAMP; }
+
+int sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+    return n;
+}
+
+shine_status check_shape(int64_t H, int64_t W, int border) {
+    if (!border_ok(border)) return SHINE_ERR_INVALID_ARG;
+    const int64_t lo = border == SHINE_VALID ? 5 : 1;
+    if (H < lo || W < lo || H > kMaxDim || W > kMaxDim) return SHINE_ERR_INVALID_ARG;
+    return SHINE_OK;
+}
+
+int choose_band_rows(int64_t rows, int64_t nseg, int64_t target_warps, int min_rows) {
+    if (rows <= 0) return 1;
+    int64_t nband = (target_warps + nseg - 1) / nseg;
+    if (nband < 1) nband = 1;
+    int64_t br = (rows + nband - 1) / nband;
+    if (br < min_rows) br = min_rows;
+    if (br > rows) br = rows;
+    return (int)br;
+}
+
+void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows) {
+    g.H = (int)H;
+    g.W = (int)W;
+    g.valid = border == SHINE_VALID;
+    if (g.valid && !full_image) {
+        g.xlo = 2; g.xhi = (int)W - 2; g.ylo = 2; g.yhi = (int)H - 2; g.ox = 2; g.oy = 2;
+    } else {
+        g.xlo = 0; g.xhi = (int)W; g.ylo = 0; g.yhi = (int)H;
+        g.ox = g.valid ? 2 : 0; g.oy = g.valid ? 2 : 0;
+    }
+    g.x0 = 0;
+    g.nseg = (g.xhi + kSegOut - 1) / kSegOut;
+    g.band_rows = band_rows;
+    g.nband = (g.yhi - g.ylo + band_rows - 1) / band_rows;
+}
+
+Geometry fwd_geometry(int64_t H, int64_t W, int border, int band_rows_override) {
+    Geometry g;
+    fill_geometry(g, H, W, border, false, 1);
+    const int64_t rows = g.yhi - g.ylo;
+    const int br = band_rows_override > 0 ? band_rows_override
+                                          : choose_band_rows(rows, g.nseg, (int64_t)sm_count() * kFwdWarpsPerSm, 16);
+    fill_geometry(g, H, W, border, false, br);
+    return g;
+}
+
+Geometry bwd_geometry(int64_t H, int64_t W, int border, int band_rows_override) {
+    Geometry g;
+    fill_geometry(g, H, W, border, true, 1);
+    const int64_t rows = g.yhi - g.ylo;
+    const int br = band_rows_override > 0 ? band_rows_override
+                                          : choose_band_rows(rows, g.nseg, (int64_t)sm_count() * kBwdWarpsPerSm, 32);
+    fill_geometry(g, H, W, border, true, br);
+    return g;
+}
+
+bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace shine
+
+using namespace shine;
+
+extern "C" {
+
+const char* shine_status_string(shine_status s) {
+    switch (s) {
+        case SHINE_OK: return "ok";
+        case SHINE_ERR_INVALID_ARG: return "invalid argument";
+        case SHINE_ERR_ALIGNMENT: return "misaligned pointer";
+        case SHINE_ERR_WORKSPACE: return "workspace missing or too small";
+        case SHINE_ERR_UNSUPPORTED: return "unsupported combination";
+        case SHINE_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+int shine_last_cuda_error(void) { return g_last_cuda_error; }
+
+shine_status shine_output_shape(int64_t H, int64_t W, shine_border border, int64_t* H_out, int64_t* W_out) {
+    if (!H_out || !W_out) return SHINE_ERR_INVALID_ARG;
+    shine_status st = check_shape(H, W, border);
+    if (st != SHINE_OK) return st;
+    *H_out = border == SHINE_VALID ? H - 4 : H;
+    *W_out = border == SHINE_VALID ? W - 4 : W;
+    return SHINE_OK;
+}
+
+shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                                shine_border border, const float* kappa, const float* wx, const float* wy,
+                                void* out, int64_t out_pitch, shine_dtype out_dt, void* stream) {
+    if (!img || !kappa || !wx || !wy || !out) return SHINE_ERR_INVALID_ARG;
+    if (!dtype_ok(dt) || !dtype_ok(out_dt)) return SHINE_ERR_INVALID_ARG;
+    if (!(out_dt == dt || out_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
+    shine_status st = check_shape(H, W, border);
+    if (st != SHINE_OK) return st;
+    const int64_t Ho = border == SHINE_VALID ? H - 4 : H, Wo = border == SHINE_VALID ? W - 4 : W;
+    if (img_pitch < 3 * W || out_pitch < Wo) return SHINE_ERR_INVALID_ARG;
+    (void)Ho;
+    const size_t si = dtype_size(dt), so = dtype_size(out_dt);
+    if (!aligned_to(img, si) || !aligned_to(out, so) || !aligned_to(kappa, 4) || !aligned_to(wx, 4) ||
+        !aligned_to(wy, 4))
+        return SHINE_ERR_ALIGNMENT;
+    FwdArgs a;
+    static_cast<Geometry&>(a) = fwd_geometry(H, W, border, 0);
+    a.img = img; a.img_pitch = img_pitch; a.out = out; a.out_pitch = out_pitch;
+    a.kappa = kappa; a.wx = wx; a.wy = wy;
+    const size_t chunk = si == 4 ? 16 : 8;
+    a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
+    a.out_vec = border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
+    return cuda_status(launch_harris_fwd(a, dt, out_dt, static_cast<cudaStream_t>(stream)));
+}
+
+shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border border, size_t* bytes) {
+    if (!bytes) return SHINE_ERR_INVALID_ARG;
+    shine_status st = check_shape(H, W, border);
+    if (st != SHINE_OK) return st;
+    Geometry g = bwd_geometry(H, W, border, 0);
+    *bytes = (size_t)kParamSlots * (size_t)g.nseg * (size_t)g.nband * sizeof(double);
+    return SHINE_OK;
+}
+
+}  // extern "C"
+
+namespace shine {
+
+static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                            shine_border border, const float* kappa, const float* wx, const float* wy,
+                            const void* grad_out, int64_t gout_pitch, shine_dtype gout_dt, void* out,
+                            int64_t out_pitch, void* grad_img, int64_t gimg_pitch, float* grad_kappa,
+                            float* grad_wx, float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+    if (!img || !kappa || !wx || !wy || !grad_out) return SHINE_ERR_INVALID_ARG;
+    if (!dtype_ok(dt) || !dtype_ok(gout_dt)) return SHINE_ERR_INVALID_ARG;
+    if (!(gout_dt == dt || gout_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
+    shine_status st = check_shape(H, W, border);
+    if (st != SHINE_OK) return st;
+    const int64_t Ho = border == SHINE_VALID ? H - 4 : H, Wo = border == SHINE_VALID ? W - 4 : W;
+    if (img_pitch < 3 * W || gout_pitch < Wo || (grad_img && gimg_pitch < 3 * W) || (out && out_pitch < Wo))
+        return SHINE_ERR_INVALID_ARG;
+    const size_t si = dtype_size(dt), sg = dtype_size(gout_dt);
+    if (!aligned_to(img, si) || !aligned_to(grad_out, sg) || (grad_img && !aligned_to(grad_img, si)) ||
+        (out && !aligned_to(out, si)) || !aligned_to(kappa, 4) || !aligned_to(wx, 4) || !aligned_to(wy, 4) ||
+        (grad_kappa && !aligned_to(grad_kappa, 4)) || (grad_wx && !aligned_to(grad_wx, 4)) ||
+        (grad_wy && !aligned_to(grad_wy, 4)))
+        return SHINE_ERR_ALIGNMENT;
+    BwdArgs a;
+    static_cast<Geometry&>(a) = bwd_geometry(H, W, border, 0);
+    const size_t need = (size_t)kParamSlots * (size_t)a.nseg * (size_t)a.nband * sizeof(double);
+    if (!workspace || ws_bytes < need) return SHINE_ERR_WORKSPACE;
+    if (!aligned_to(workspace, 16)) return SHINE_ERR_ALIGNMENT;
+    if (!out && !grad_img && !grad_kappa && !grad_wx && !grad_wy) return SHINE_OK;
+    a.img = img; a.img_pitch = img_pitch;
+    a.gout = grad_out; a.gout_pitch = gout_pitch; a.gho = (int)Ho; a.gwo = (int)Wo;
+    a.gimg = grad_img; a.gimg_pitch = gimg_pitch;
+    a.kappa = kappa; a.wx = wx; a.wy = wy;
+    a.partials = static_cast<double*>(workspace);
+    const size_t chunk = si == 4 ? 16 : 8;
+    a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
+    a.g_aligned = border == SHINE_CLAMP && aligned_to(grad_out, 4 * sg) && ((size_t)gout_pitch * sg) % (4 * sg) == 0;
+    a.gimg_vec = grad_img && aligned_to(grad_img, chunk) && ((size_t)gimg_pitch * si) % chunk == 0;
+    a.rout = out; a.rout_pitch = out_pitch;
+    a.rout_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * si) && ((size_t)out_pitch * si) % (4 * si) == 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = cuda_status(launch_harris_bwd(a, dt, gout_dt, s));
+    if (st != SHINE_OK) return st;
+    if (grad_kappa || grad_wx || grad_wy)
+        st = cuda_status(launch_finalize_params(a.partials, (int64_t)a.nseg * a.nband, grad_kappa, grad_wx, grad_wy, s));
+    return st;
+}
+
+}  // namespace shine
+
+extern "C" {
+
+shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                                shine_border border, const float* kappa, const float* wx, const float* wy,
+                                const void* grad_out, int64_t gout_pitch, shine_dtype gout_dt, void* grad_img,
+                                int64_t gimg_pitch, float* grad_kappa, float* grad_wx, float* grad_wy,
+                                void* workspace, size_t ws_bytes, void* stream) {
+    return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, gout_dt, nullptr, 0,
+                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
+}
+
+shine_status shine_pipeline_fwd_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                                    shine_border border, const float* kappa, const float* wx, const float* wy,
+                                    const void* grad_out, int64_t gout_pitch, void* out, int64_t out_pitch,
+                                    void* grad_img, int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
+                                    float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+    return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, dt, out, out_pitch,
+                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"

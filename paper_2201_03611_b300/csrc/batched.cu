@@ -1,0 +1,410 @@
+// Many images of different sizes in one persistent launch.
+//
+// The plan cuts every image into warp work items -- (image, column segment, row band) tiles,
+// the same items the single-image kernels use -- with a band height chosen per shape bucket
+// (from a tuning cache written by paper_2201_03611_b300/tune.py, else a built-in rule). The
+// tiles are ordered longest first; a persistent grid (one resident set of CTAs per SM) claims
+// them warp by warp from an atomic counter in the workspace. Each tile writes its own
+// parameter-cotangent partials at its fixed index, and a separate kernel sums them in a fixed
+// order (per image for d kappa_i, over all tiles for d Wx, d Wy), so results do not depend on
+// which warp ran which tile. There are no inter-CTA waits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "harris_bwd_strip.cuh"
+#include "harris_fwd_strip.cuh"
+#include "shine.h"
+#include "shine_host.h"
+
+struct shine_plan {
+    int n = 0;
+    int dt = 0;
+    int border = 0;
+    int mode = 0;
+    int ntiles = 0;
+    int grid = 0;
+    std::vector<int64_t> H, W;
+    std::vector<int> band_rows;
+    std::vector<int> tile_begin;  // [n + 1], image-major tile ids
+    void* dbuf = nullptr;         // device: tiles (int4 x ntiles) | band_rows (n) | tile_begin (n+1)
+    int4* d_tiles = nullptr;
+    int* d_band_rows = nullptr;
+    int* d_tile_begin = nullptr;
+};
+
+namespace shine {
+
+namespace {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchStages = 4;
+
+struct BatchArgs {
+    const shine_image_desc* descs;
+    const int4* tiles;       // (image, seg, band, tile id) in claim order
+    const int* band_rows;    // per image
+    int ntiles;
+    int n;
+    int valid;
+    unsigned int* counter;
+    double* partials;        // [kParamSlots][ntiles]
+    const float* kappa;      // [n]
+    const float* wx;
+    const float* wy;
+};
+
+__device__ __forceinline__ void dev_geometry(Geometry& g, int H, int W, int valid, bool full_image, int br) {
+    g.H = H; g.W = W; g.valid = valid;
+    if (valid && !full_image) {
+        g.xlo = 2; g.xhi = W - 2; g.ylo = 2; g.yhi = H - 2; g.ox = 2; g.oy = 2;
+    } else {
+        g.xlo = 0; g.xhi = W; g.ylo = 0; g.yhi = H; g.ox = valid ? 2 : 0; g.oy = valid ? 2 : 0;
+    }
+    g.x0 = 0;
+    g.nseg = (g.xhi + kSegOut - 1) / kSegOut;
+    g.band_rows = br;
+    g.nband = (g.yhi - g.ylo + br - 1) / br;
+}
+
+__device__ __forceinline__ bool dev_aligned(const void* p, int64_t pitch, size_t esize, size_t chunk) {
+    return (reinterpret_cast<uintptr_t>(p) % chunk) == 0 && ((size_t)pitch * esize) % chunk == 0;
+}
+
+template <typename T, bool FWD_BWD>
+__global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NS = kBatchStages;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int tid = warp * 32 + lane;
+    T* ring = reinterpret_cast<T*>(smem_raw) + tid * NS * 12;
+    T* gring = reinterpret_cast<T*>(smem_raw + (size_t)kBatchThreads * NS * 12 * sizeof(T)) + tid * NS * 4;
+    constexpr size_t chunk = sizeof(T) == 4 ? 16 : 8;
+    const bool producer = lane >= 1 && lane <= 30;
+    Params P;
+    load_params(P, b.wx, b.wy, b.kappa);  // kappa replaced per tile below
+
+    for (;;) {
+        unsigned int t = 0;
+        if (lane == 0) t = atomicAdd(b.counter, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= (unsigned)b.ntiles) break;
+        const int4 tile = b.tiles[t];
+        const int img = tile.x, seg = tile.y, band = tile.z, tile_id = tile.w;
+        const shine_image_desc d = b.descs[img];
+        P.kappa = __ldg(b.kappa + img);
+        const int H = (int)d.H, W = (int)d.W;
+        if constexpr (!FWD_BWD) {
+            FwdArgs a;
+            dev_geometry(a, H, W, b.valid, false, b.band_rows[img]);
+            a.img = d.img; a.img_pitch = d.img_pitch; a.out = d.out; a.out_pitch = d.out_pitch;
+            a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
+            a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);
+            a.out_vec = !b.valid && dev_aligned(d.out, d.out_pitch, sizeof(T), 4 * sizeof(T));
+            const int xb = seg * kSegOut, x = xb - 4 + 4 * lane;
+            const int y0 = a.ylo + band * a.band_rows, y1 = min(y0 + a.band_rows, a.yhi);
+            const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > W) || a.valid;
+            if (a.aligned) {
+                if (edge) fwd_strip<T, T, NS, true, true>(a, P, lane, x, y0, y1, ring);
+                else fwd_strip<T, T, NS, false, true>(a, P, lane, x, y0, y1, ring);
+            } else {
+                fwd_strip<T, T, NS, true, false>(a, P, lane, x, y0, y1, ring);
+            }
+        } else {
+            BwdArgs a;
+            dev_geometry(a, H, W, b.valid, true, b.band_rows[img]);
+            a.img = d.img; a.img_pitch = d.img_pitch;
+            a.gout = d.grad_out; a.gout_pitch = d.gout_pitch;
+            a.gho = b.valid ? H - 4 : H; a.gwo = b.valid ? W - 4 : W;
+            a.gimg = d.grad_img; a.gimg_pitch = d.gimg_pitch;
+            a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
+            a.partials = nullptr;
+            a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);
+            a.g_aligned = !b.valid && dev_aligned(d.grad_out, d.gout_pitch, sizeof(T), 4 * sizeof(T));
+            a.gimg_vec = d.grad_img != nullptr && dev_aligned(d.grad_img, d.gimg_pitch, sizeof(T), chunk);
+            const bool rvec = d.out != nullptr && dev_aligned(d.out, d.out_pitch, sizeof(T), 4 * sizeof(T));
+            const int xb = seg * kSegOut, x = xb - 4 + 4 * lane;
+            const int y0 = band * a.band_rows, y1 = min(y0 + a.band_rows, H);
+            const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > W);
+            float acc[kParamSlots];
+#pragma unroll
+            for (int i = 0; i < kParamSlots; ++i) acc[i] = 0.0f;
+            T* rout = static_cast<T*>(d.out);
+            if (a.aligned && a.g_aligned) {
+                if (edge)
+                    bwd_strip<T, T, NS, true, true, true, true>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
+                                                                d.out_pitch, rvec);
+                else
+                    bwd_strip<T, T, NS, false, true, true, true>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
+                                                                 d.out_pitch, rvec);
+            } else {
+                bwd_strip<T, T, NS, true, false, false, true>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
+                                                              d.out_pitch, rvec);
+            }
+#pragma unroll
+            for (int i = 0; i < kParamSlots; ++i) {
+                double v = producer ? (double)acc[i] : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+                if (lane == 0) b.partials[(int64_t)i * b.ntiles + tile_id] = v;
+            }
+        }
+    }
+}
+
+// Fixed-order sums: block i < n -> d kappa_i over image i's tiles; block n + f -> d W slot f.
+__global__ void __launch_bounds__(256) finalize_batched_kernel(const double* partials, int ntiles, int n,
+                                                               const int* tile_begin, float* gkappa, float* gwx,
+                                                               float* gwy) {
+    __shared__ double red[256];
+    const int blk = blockIdx.x;
+    int f, lo, hi;
+    if (blk < n) { f = 0; lo = tile_begin[blk]; hi = tile_begin[blk + 1]; }
+    else { f = 1 + (blk - n); lo = 0; hi = ntiles; }
+    double s = 0.0;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += 256) s += partials[(int64_t)f * ntiles + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float v = (float)red[0];
+        if (blk < n) { if (gkappa) gkappa[blk] = v; }
+        else if (f < 10) { if (gwx) gwx[f - 1] = v; }
+        else { if (gwy) gwy[f - 10] = v; }
+    }
+}
+
+template <typename T, bool FWD_BWD>
+size_t batched_smem() {
+    return (size_t)kBatchThreads * kBatchStages * (12 + (FWD_BWD ? 4 : 0)) * sizeof(T);
+}
+
+template <typename T, bool FWD_BWD>
+int batched_grid() {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harris_batched_kernel<T, FWD_BWD>, kBatchThreads,
+                                                      batched_smem<T, FWD_BWD>()) != cudaSuccess ||
+        per_sm <= 0)
+        per_sm = 1;
+    return per_sm * sm_count();
+}
+
+template <typename T, bool FWD_BWD>
+cudaError_t launch_batched_t(const BatchArgs& b, int grid, cudaStream_t s) {
+    harris_batched_kernel<T, FWD_BWD><<<grid, kBatchThreads, batched_smem<T, FWD_BWD>(), s>>>(b);
+    return cudaPeekAtLastError();
+}
+
+int grid_for(int dt, int mode) {
+    const bool fb = mode == SHINE_MODE_FWD_BWD;
+    switch (dt) {
+        case SHINE_F32: return fb ? batched_grid<float, true>() : batched_grid<float, false>();
+        case SHINE_BF16: return fb ? batched_grid<__nv_bfloat16, true>() : batched_grid<__nv_bfloat16, false>();
+        default: return fb ? batched_grid<__half, true>() : batched_grid<__half, false>();
+    }
+}
+
+cudaError_t launch_batched(const BatchArgs& b, int dt, int mode, int grid, cudaStream_t s) {
+    const bool fb = mode == SHINE_MODE_FWD_BWD;
+    switch (dt) {
+        case SHINE_F32: return fb ? launch_batched_t<float, true>(b, grid, s) : launch_batched_t<float, false>(b, grid, s);
+        case SHINE_BF16:
+            return fb ? launch_batched_t<__nv_bfloat16, true>(b, grid, s)
+                      : launch_batched_t<__nv_bfloat16, false>(b, grid, s);
+        default: return fb ? launch_batched_t<__half, true>(b, grid, s) : launch_batched_t<__half, false>(b, grid, s);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Band heights: shape bucket = ceil(log2(rows)), looked up in the tuning cache (text lines
+// "<gpu> <dtype> <border> <mode> <bucket> <band_rows>"), else a built-in rule.
+// ---------------------------------------------------------------------------------------------
+int bucket_of(int64_t rows) {
+    int b = 0;
+    while ((int64_t(1) << b) < rows) ++b;
+    return b;
+}
+
+std::string gpu_key() {
+    int dev = 0;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    std::string name = p.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    int rt = 0;
+    cudaRuntimeGetVersion(&rt);
+    return name + "/sm" + std::to_string(p.major * 10 + p.minor) + "/" + std::to_string(p.multiProcessorCount) +
+           "sm/cuda" + std::to_string(rt);
+}
+
+struct TuneEntry {
+    int bucket, rows;
+};
+
+std::vector<TuneEntry> read_tune_cache(const char* path, int dt, int border, int mode) {
+    std::vector<TuneEntry> out;
+    if (!path) return out;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return out;
+    const std::string key = gpu_key();
+    char gk[256];
+    int d, b, m, bucket, rows;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        if (std::sscanf(line, "%255s %d %d %d %d %d", gk, &d, &b, &m, &bucket, &rows) == 6 && key == gk && d == dt &&
+            b == border && m == mode && rows > 0)
+            out.push_back({bucket, rows});
+    }
+    std::fclose(f);
+    return out;
+}
+
+int default_band_rows(int64_t rows, int mode) {
+    // long bands keep the vertical halo (4 or 8 recomputed rows per band) small; short ones
+    // balance the tail of the persistent schedule
+    const int64_t target = mode == SHINE_MODE_FWD_BWD ? 256 : 128;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(rows, target));
+}
+
+}  // namespace
+
+}  // namespace shine
+
+using namespace shine;
+
+extern "C" {
+
+shine_status shine_plan_create(const int64_t* HW, int32_t n, shine_dtype dt, shine_border border, int32_t mode,
+                               const char* tune_cache_path, shine_plan** plan) {
+    if (!HW || n <= 0 || !plan || !dtype_ok(dt) || !border_ok(border)) return SHINE_ERR_INVALID_ARG;
+    if (mode != SHINE_MODE_FWD && mode != SHINE_MODE_FWD_BWD) return SHINE_ERR_INVALID_ARG;
+    *plan = nullptr;
+    shine_plan* p = new (std::nothrow) shine_plan();
+    if (!p) return SHINE_ERR_INVALID_ARG;
+    p->n = n; p->dt = dt; p->border = border; p->mode = mode;
+    const std::vector<TuneEntry> tuned = read_tune_cache(tune_cache_path, dt, border, mode);
+    struct Item { int img, seg, band, id, work; };
+    std::vector<Item> items;
+    p->tile_begin.push_back(0);
+    for (int i = 0; i < n; ++i) {
+        const int64_t H = HW[2 * i], W = HW[2 * i + 1];
+        if (check_shape(H, W, border) != SHINE_OK) { delete p; return SHINE_ERR_INVALID_ARG; }
+        p->H.push_back(H);
+        p->W.push_back(W);
+        Geometry g;
+        fill_geometry(g, H, W, border, mode == SHINE_MODE_FWD_BWD, 1);
+        const int64_t rows = g.yhi - g.ylo;
+        int br = default_band_rows(rows, mode);
+        const int bk = bucket_of(rows);
+        for (const TuneEntry& e : tuned)
+            if (e.bucket == bk) br = (int)std::max<int64_t>(1, std::min<int64_t>(rows, e.rows));
+        p->band_rows.push_back(br);
+        fill_geometry(g, H, W, border, mode == SHINE_MODE_FWD_BWD, br);
+        const int halo = mode == SHINE_MODE_FWD_BWD ? 8 : 4;
+        for (int band = 0; band < g.nband; ++band) {
+            const int y0 = g.ylo + band * br, y1 = std::min(y0 + br, g.yhi);
+            for (int seg = 0; seg < g.nseg; ++seg) {
+                const int id = (int)items.size();
+                items.push_back({i, seg, band, id, (y1 - y0) + halo});
+            }
+        }
+        if (items.size() > (size_t)(1 << 30)) { delete p; return SHINE_ERR_INVALID_ARG; }
+        p->tile_begin.push_back((int)items.size());
+    }
+    p->ntiles = (int)items.size();
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
+    std::vector<int4> tiles(items.size());
+    for (size_t t = 0; t < items.size(); ++t) tiles[t] = make_int4(items[t].img, items[t].seg, items[t].band, items[t].id);
+    const size_t bytes_tiles = tiles.size() * sizeof(int4);
+    const size_t bytes_br = (size_t)n * sizeof(int);
+    const size_t off_br = (bytes_tiles + 255) / 256 * 256;
+    const size_t off_tb = off_br + (bytes_br + 255) / 256 * 256;
+    const size_t total = off_tb + (size_t)(n + 1) * sizeof(int);
+    if (cudaMalloc(&p->dbuf, total) != cudaSuccess) { delete p; return cuda_status(cudaGetLastError()); }
+    char* base = static_cast<char*>(p->dbuf);
+    p->d_tiles = reinterpret_cast<int4*>(base);
+    p->d_band_rows = reinterpret_cast<int*>(base + off_br);
+    p->d_tile_begin = reinterpret_cast<int*>(base + off_tb);
+    cudaError_t e = cudaMemcpy(p->d_tiles, tiles.data(), bytes_tiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_band_rows, p->band_rows.data(), bytes_br, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_tile_begin, p->tile_begin.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(p->dbuf); delete p; return cuda_status(e); }
+    p->grid = grid_for(dt, mode);
+    *plan = p;
+    return SHINE_OK;
+}
+
+shine_status shine_plan_workspace(const shine_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return SHINE_ERR_INVALID_ARG;
+    *bytes = 256 + (size_t)kParamSlots * (size_t)plan->ntiles * sizeof(double);
+    return SHINE_OK;
+}
+
+shine_status shine_plan_tile_rows(const shine_plan* plan, int32_t i, int32_t* rows) {
+    if (!plan || !rows || i < 0 || i >= plan->n) return SHINE_ERR_INVALID_ARG;
+    *rows = plan->band_rows[i];
+    return SHINE_OK;
+}
+
+shine_status shine_pipeline_batched(const shine_plan* plan, const shine_image_desc* descs, const float* kappa,
+                                    const float* wx, const float* wy, float* grad_kappa, float* grad_wx,
+                                    float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+    if (!plan || !descs || !kappa || !wx || !wy) return SHINE_ERR_INVALID_ARG;
+    size_t need = 0;
+    shine_plan_workspace(plan, &need);
+    if (!workspace || ws_bytes < need) return SHINE_ERR_WORKSPACE;
+    if (!aligned_to(workspace, 256) || !aligned_to(descs, 8) || !aligned_to(kappa, 4)) return SHINE_ERR_ALIGNMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchArgs b;
+    b.descs = descs;
+    b.tiles = plan->d_tiles;
+    b.band_rows = plan->d_band_rows;
+    b.ntiles = plan->ntiles;
+    b.n = plan->n;
+    b.valid = plan->border == SHINE_VALID;
+    b.counter = static_cast<unsigned int*>(workspace);
+    b.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + 256);
+    b.kappa = kappa; b.wx = wx; b.wy = wy;
+    shine_status st = cuda_status(cudaMemsetAsync(b.counter, 0, sizeof(unsigned int), s));
+    if (st != SHINE_OK) return st;
+    st = cuda_status(launch_batched(b, plan->dt, plan->mode, plan->grid, s));
+    if (st != SHINE_OK) return st;
+    if (plan->mode == SHINE_MODE_FWD_BWD && (grad_kappa || grad_wx || grad_wy)) {
+        finalize_batched_kernel<<<plan->n + kParamSlots - 1, 256, 0, s>>>(b.partials, plan->ntiles, plan->n,
+                                                                        plan->d_tile_begin, grad_kappa, grad_wx,
+                                                                        grad_wy);
+        st = cuda_status(cudaPeekAtLastError());
+    }
+    return st;
+}
+
+int shine_tune_key(char* buf, size_t len) {
+    const std::string k = gpu_key();
+    if (k == "unknown") return -1;
+    if (buf && len > 0) {
+        std::strncpy(buf, k.c_str(), len - 1);
+        buf[len - 1] = '\0';
+    }
+    return (int)k.size();
+}
+
+void shine_plan_destroy(shine_plan* plan) {
+    if (!plan) return;
+    if (plan->dbuf) cudaFree(plan->dbuf);
+    delete plan;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Fused adjoint kernel of the Harris pipeline: the vector-Jacobian product of
+// L = sum(g * R) with respect to the image, kappa and the two 3x3 weight matrices.
+//
+// Reverse mode through the patterns of the forward pass, with each pattern replaced by its
+// adjoint (map -> pointwise chain rule, reduce(+) -> broadcast, slide2D -> overlap-add,
+// pad_clamp -> fold onto the clamped index, a shared parameter -> sum over every use):
+//
+//   B1  recompute G, Ix, Iy and S (nothing of the forward pass is stored)
+//   B2  gS = (g (Syy - 2 kappa T), -2 g Sxy, g (Sxx - 2 kappa T)),  d kappa += -g T^2
+//   B3  gP = adjoint of the clamped 3x3 box sum applied to gS. For the all-ones symmetric
+//       window with clamp padding this adjoint equals the clamped box sum itself: on an axis
+//       of length n, the number of taps d in {-1,0,1} with clamp(p+d) = q equals the number
+//       with clamp(q+d) = p for every p, q.
+//   B4  gIx = 2 Ix gPxx + Iy gPxy,  gIy = Ix gPxy + 2 Iy gPyy
+//   B5  gG = transposed 3x3 stencil of (gIx, gIy) with Wx, Wy on the clamp-padded domain,
+//       folded back: the padded row/column -1 is added to row/column 0, and H (W) to H-1
+//       (W-1);  d W[a][b] += gI(p) * G(clamp(p + (a-1, b-1)))
+//   B6  d img[c] = coef_c * gG
+//
+// A warp streams one (column segment, row band): per step it stages image row r and
+// cotangent row r-2, and writes d img row r-4 (the dependency reaches 4 rows and 4 columns:
+// one per stencil, forward and adjoint). Lanes 0 and 31 supply exactly the 4-column halo.
+// Parameter cotangents are accumulated per lane in float32, reduced per warp in float64 and
+// summed in a fixed order by the finalize kernel, so every run gives the same bits.
+#include "harris_bwd_strip.cuh"
+
+namespace shine {
+
+namespace {
+
+template <typename TI, typename TG, int NS, bool ALIGNED, bool GALIGNED, bool WITH_R>
+__global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (kBwdThreads / 32) + warp;
+    const int nwarps = a.nseg * a.nband;
+    if (gw >= nwarps) return;  // whole warp
+    const int seg = gw % a.nseg;
+    const int band = gw / a.nseg;
+    const int xb = a.x0 + seg * kSegOut;
+    const int x = xb - 4 + 4 * lane;
+    const int y0 = a.ylo + band * a.band_rows;
+    const int y1 = min(y0 + a.band_rows, a.yhi);
+    const int tid = warp * 32 + lane;
+    TI* ring = reinterpret_cast<TI*>(smem_raw) + tid * NS * 12;
+    TG* gring = reinterpret_cast<TG*>(smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI)) + tid * NS * 4;
+    Params P;
+    load_params(P, a.wx, a.wy, a.kappa);
+    float acc[kParamSlots];
+#pragma unroll
+    for (int i = 0; i < kParamSlots; ++i) acc[i] = 0.0f;
+    const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W);
+    TI* rout = static_cast<TI*>(a.rout);
+    if (edge)
+        bwd_strip<TI, TG, NS, true, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
+                                                               a.rout_pitch, a.rout_vec);
+    else
+        bwd_strip<TI, TG, NS, false, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
+                                                                a.rout_pitch, a.rout_vec);
+    // Warp partials in float64, lanes 0 and 31 excluded by selection (their values may be
+    // unrelated to this warp's pixels).
+    const bool producer = lane >= 1 && lane <= 30;
+#pragma unroll
+    for (int i = 0; i < kParamSlots; ++i) {
+        double v = producer ? (double)acc[i] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) a.partials[(int64_t)i * nwarps + gw] = v;
+    }
+}
+
+template <typename TI, typename TG>
+cudaError_t launch_bwd_t(const BwdArgs& a, cudaStream_t s) {
+    constexpr int NS = kBwdStages;
+    const int64_t warps = (int64_t)a.nseg * a.nband;
+    const int64_t blocks = (warps + kBwdThreads / 32 - 1) / (kBwdThreads / 32);
+    const size_t smem = (size_t)kBwdThreads * NS * (12 * sizeof(TI) + 4 * sizeof(TG));
+    if (blocks <= 0) return cudaSuccess;
+#define SHINE_BWD_LAUNCH(AL, GA, WR) \
+    harris_bwd_kernel<TI, TG, NS, AL, GA, WR><<<(unsigned)blocks, kBwdThreads, smem, s>>>(a)
+    const bool wr = a.rout != nullptr;
+    if (a.aligned && a.g_aligned) {
+        if (wr) SHINE_BWD_LAUNCH(true, true, true); else SHINE_BWD_LAUNCH(true, true, false);
+    } else if (a.aligned) {
+        if (wr) SHINE_BWD_LAUNCH(true, false, true); else SHINE_BWD_LAUNCH(true, false, false);
+    } else {
+        if (wr) SHINE_BWD_LAUNCH(false, false, true); else SHINE_BWD_LAUNCH(false, false, false);
+    }
+#undef SHINE_BWD_LAUNCH
+    return cudaPeekAtLastError();
+}
+
+// Fixed-order float64 sum of the per-warp partials: block f reduces slot f.
+__global__ void __launch_bounds__(256) finalize_params_kernel(const double* partials, int64_t n, float* gk,
+                                                              float* gwx, float* gwy) {
+    __shared__ double red[256];
+    const int f = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += partials[(int64_t)f * n + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float v = (float)red[0];
+        if (f == 0) { if (gk) *gk = v; }
+        else if (f < 10) { if (gwx) gwx[f - 1] = v; }
+        else { if (gwy) gwy[f - 10] = v; }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_harris_bwd(const BwdArgs& a, int dt, int gout_dt, cudaStream_t s) {
+#define SHINE_BWD_CASE(I, G, TI, TG) \
+    if (dt == I && gout_dt == G) return launch_bwd_t<TI, TG>(a, s);
+    SHINE_BWD_CASE(0, 0, float, float)
+    SHINE_BWD_CASE(1, 1, __nv_bfloat16, __nv_bfloat16)
+    SHINE_BWD_CASE(2, 2, __half, __half)
+    SHINE_BWD_CASE(1, 0, __nv_bfloat16, float)
+    SHINE_BWD_CASE(2, 0, __half, float)
+#undef SHINE_BWD_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize_params(const double* partials, int64_t n, float* gkappa, float* gwx, float* gwy,
+                                   cudaStream_t s) {
+    finalize_params_kernel<<<kParamSlots, 256, 0, s>>>(partials, n, gkappa, gwx, gwy);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace shine

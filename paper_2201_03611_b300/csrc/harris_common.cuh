@@ -1,0 +1,257 @@
+// Device building blocks shared by the fused Harris kernels (sm_103a).
+//
+// Work decomposition (the split/join tiling of the paper's Sec. 4.2, lowered by hand):
+//   * the image is cut into column segments of kSegOut = 120 output columns; one warp owns a
+//     segment and a band of rows, and streams down the band row by row (a sequential map over
+//     rows, the mapSeq choice of Sec. 4.2), keeping the 3-row stencil windows in registers;
+//   * each lane owns kCols = 4 adjacent columns; lanes 1..30 produce output, lanes 0 and 31
+//     only provide the 2-column halo each stencil needs (read from neighbours by warp
+//     shuffles, so no shared-memory round trip and no block-wide barrier is needed);
+//   * the lane's 4 input pixels of each row are staged through a per-lane ring of NS rows in
+//     shared memory with cp.async (the toMem(Local) choice), so NS-1 rows are always in
+//     flight while the current one is computed;
+//   * per-stage clamp padding is applied where it matters: at the image border, the value a
+//     stencil reads beyond the edge is replaced by the edge value of THAT stage (gray, the
+//     vertical product sums, ...), which is exactly pad_clamp before each slide2D.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "harris_kernels.h"
+
+namespace shine {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Luminance weights of A1 (nearest float32 values of 0.299, 0.587, 0.114).
+constexpr float kGrayR = 0.299f, kGrayG = 0.587f, kGrayB = 0.114f;
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// ---------------------------------------------------------------------------------------------
+// Storage types: float32 arithmetic, float32 / bf16 / fp16 storage (round to nearest even).
+// ---------------------------------------------------------------------------------------------
+template <typename T> struct Conv;
+template <> struct Conv<float> {
+    __device__ __forceinline__ static float ld(float v) { return v; }
+    __device__ __forceinline__ static float st(float v) { return v; }
+};
+template <> struct Conv<__nv_bfloat16> {
+    __device__ __forceinline__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct Conv<__half> {
+    __device__ __forceinline__ static float ld(__half v) { return __half2float(v); }
+    __device__ __forceinline__ static __half st(float v) { return __float2half_rn(v); }
+};
+
+// 16-bit types are moved as raw bits.
+template <typename T> struct Bits16;
+template <> struct Bits16<__nv_bfloat16> {
+    __device__ __forceinline__ static float to_f(uint32_t b16) { return __uint_as_float(b16 << 16); }
+};
+template <> struct Bits16<__half> {
+    __device__ __forceinline__ static float to_f(uint32_t b16) {
+        return __half2float(__ushort_as_half((unsigned short)b16));
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// cp.async (LDGSTS) helpers. src_bytes < cp-size zero-fills the rest of the chunk and reads
+// only src_bytes from global memory.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// PixelRows: the lane's 4 pixels (12 elements) of successive image rows.
+//   ALIGNED: staged through a per-lane ring of NS rows in shared memory with cp.async; the
+//            image pointer and the row pitch in bytes are multiples of the chunk size
+//            (16 bytes for float32, 8 bytes for 16-bit types).
+//   !ALIGNED: read element by element from global memory when needed (slow path).
+// EDGE: some of the lane's pixels may lie outside [0, W): those read as zero and are never
+// read from memory.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NS, bool EDGE, bool ALIGNED>
+struct PixelRows {
+    static constexpr int kChunk = sizeof(T) == 4 ? 16 : 8;
+    T* ring;         // this lane's NS x 12 elements
+    const T* img;
+    int64_t pitch;   // elements
+    int x;           // first column of the lane
+    int W;
+    int valid_bytes; // bytes of the lane's 12 elements inside the row (EDGE only)
+
+    __device__ __forceinline__ PixelRows(T* ring_, const T* img_, int64_t pitch_, int x_, int W_)
+        : ring(ring_), img(img_), pitch(pitch_), x(x_), W(W_) {
+        int npx = x < 0 ? 0 : (W - x >= kCols ? kCols : (W - x > 0 ? W - x : 0));
+        valid_bytes = npx * 3 * (int)sizeof(T);
+    }
+
+    // Start staging image row yc (already clamped to [0, H)) into ring slot `slot`.
+    __device__ __forceinline__ void fetch(int slot, int yc) const {
+        if constexpr (ALIGNED) {
+            const char* src = reinterpret_cast<const char*>(img + (int64_t)yc * pitch + (int64_t)x * 3);
+            uint32_t dst = smem_u32(ring + slot * 12);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                int nb = kChunk;
+                const char* s = src + i * kChunk;
+                if constexpr (EDGE) {
+                    nb = valid_bytes - i * kChunk;
+                    nb = nb < 0 ? 0 : (nb > kChunk ? kChunk : nb);
+                    if (nb == 0) s = reinterpret_cast<const char*>(img);
+                }
+                if constexpr (kChunk == 16) cp_async16(dst + i * 16, s, nb);
+                else cp_async8(dst + i * 8, s, nb);
+            }
+        }
+    }
+
+    // The 12 channel values (float32) of the lane's pixels in image row yc (slot for ALIGNED).
+    __device__ __forceinline__ void read(int slot, int yc, float v[12]) const {
+        if constexpr (ALIGNED) {
+            if constexpr (sizeof(T) == 4) {
+                const float4* s = reinterpret_cast<const float4*>(ring + slot * 12);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float4 q = s[i];
+                    v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+                }
+            } else {
+                const uint2* s = reinterpret_cast<const uint2*>(ring + slot * 12);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    uint2 q = s[i];
+                    v[4 * i] = Bits16<T>::to_f(q.x & 0xffffu);
+                    v[4 * i + 1] = Bits16<T>::to_f(q.x >> 16);
+                    v[4 * i + 2] = Bits16<T>::to_f(q.y & 0xffffu);
+                    v[4 * i + 3] = Bits16<T>::to_f(q.y >> 16);
+                }
+            }
+        } else {
+            const T* row = img + (int64_t)yc * pitch;
+#pragma unroll
+            for (int j = 0; j < kCols; ++j) {
+                int c = x + j;
+                bool in = !EDGE || (c >= 0 && c < W);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    v[3 * j + ch] = in ? Conv<T>::ld(row[(int64_t)c * 3 + ch]) : 0.0f;
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Warp-level neighbour exchange and per-stage clamp at the image border.
+// A "row6" holds the 6 values of columns x-1 .. x+4 of one stage: the lane's own 4 and one
+// from each neighbouring lane.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void make_row6(const float c[4], float r6[6]) {
+    r6[0] = __shfl_up_sync(kFull, c[3], 1);
+    r6[1] = c[0]; r6[2] = c[1]; r6[3] = c[2]; r6[4] = c[3];
+    r6[5] = __shfl_down_sync(kFull, c[0], 1);
+}
+
+// pad_clamp at this stage: the value at column -1 becomes the value at column 0 and the
+// value at column W becomes the value at column W-1. Only the stencil reads of in-image
+// columns matter, and those read at most one column beyond the edge.
+__device__ __forceinline__ void clamp_row6(float r6[6], int x, int W) {
+    if (x == 0) r6[0] = r6[1];
+#pragma unroll
+    for (int p = 1; p < 6; ++p)
+        if (x - 1 + p == W) r6[p] = r6[p - 1];
+}
+
+__device__ __forceinline__ float gray_of(float r, float g, float b) {
+    return fmaf(kGrayB, b, fmaf(kGrayG, g, kGrayR * r));
+}
+
+// Loop-invariant parameters, read once per warp from device memory.
+struct Params {
+    float wx[9], wy[9], kappa;
+};
+
+__device__ __forceinline__ void load_params(Params& P, const float* wx, const float* wy, const float* kappa) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { P.wx[i] = __ldg(wx + i); P.wy[i] = __ldg(wy + i); }
+    P.kappa = __ldg(kappa);
+}
+
+// A2 on one lane: Sobel correlation of three 6-wide gray rows (r0 = row above) at the lane's
+// 4 columns, written with explicit fused multiply-adds so every kernel that calls it gets the
+// same bits.
+__device__ __forceinline__ void sobel(const Params& P, const float r0[6], const float r1[6], const float r2[6],
+                                      float ix[4], float iy[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float ax = 0.0f, ay = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ax = fmaf(P.wx[b], r0[j + b], ax);
+            ay = fmaf(P.wy[b], r0[j + b], ay);
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ax = fmaf(P.wx[3 + b], r1[j + b], ax);
+            ay = fmaf(P.wy[3 + b], r1[j + b], ay);
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ax = fmaf(P.wx[6 + b], r2[j + b], ax);
+            ay = fmaf(P.wy[6 + b], r2[j + b], ay);
+        }
+        ix[j] = ax;
+        iy[j] = ay;
+    }
+}
+
+// A3 + vertical half of A4: the three product sums over Sobel rows a (above), m, b (below),
+// each already clamped by the caller: v = a*a' + b*b' + m*m' per plane.
+__device__ __forceinline__ void vertical_products(const float ax[4], const float ay[4], const float mx[4],
+                                                  const float my[4], const float bx[4], const float by[4],
+                                                  float v[3][4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[0][j] = fmaf(ax[j], ax[j], fmaf(bx[j], bx[j], __fmul_rn(mx[j], mx[j])));
+        v[1][j] = fmaf(ax[j], ay[j], fmaf(bx[j], by[j], __fmul_rn(mx[j], my[j])));
+        v[2][j] = fmaf(ay[j], ay[j], fmaf(by[j], by[j], __fmul_rn(my[j], my[j])));
+    }
+}
+
+// Horizontal half of A4 on one plane (with the per-stage clamp on EDGE warps).
+template <bool EDGE>
+__device__ __forceinline__ void horizontal_box(const float v[4], float s[4], int x, int W) {
+    float r6[6];
+    make_row6(v, r6);
+    if constexpr (EDGE) clamp_row6(r6, x, W);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = __fadd_rn(__fadd_rn(r6[j], r6[j + 1]), r6[j + 2]);
+}
+
+// A5 in float32 (det - kappa * trace^2 cancels, so it is never done in a narrower type).
+__device__ __forceinline__ float response(float sxx, float sxy, float syy, float kappa) {
+    const float tr = __fadd_rn(sxx, syy);
+    const float det = fmaf(sxx, syy, -__fmul_rn(sxy, sxy));
+    return fmaf(-__fmul_rn(kappa, tr), tr, det);
+}
+
+}  // namespace shine

@@ -1,0 +1,73 @@
+// Host-visible launch descriptors of the Harris kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace shine {
+
+constexpr int kCols = 4;                       // pixels per lane
+constexpr int kLanes = 32;
+constexpr int kSegLoad = kLanes * kCols;       // 128 staged columns per warp segment
+constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp segment
+constexpr int kFwdThreads = 128;  // 4 warps per CTA
+constexpr int kFwdStages = 4;     // staged image rows per lane (cp.async ring)
+constexpr int kBwdThreads = 128;
+constexpr int kBwdStages = 4;
+constexpr int kParamSlots = 19;   // d kappa, d Wx[9], d Wy[9]
+
+// Geometry shared by all kernels: which output region of the image a launch covers and how
+// it is cut into (column segment, row band) work items of one warp each.
+struct Geometry {
+    int H, W;          // image size
+    int valid;         // 1: VALID borders (output (H-4)x(W-4)), 0: CLAMP (output HxW)
+    int xlo, xhi;      // output columns, in image coordinates: [xlo, xhi)
+    int ylo, yhi;      // output rows, in image coordinates: [ylo, yhi)
+    int ox, oy;        // image coordinates of output element (0, 0)
+    int x0;            // first output column of segment 0 (image coordinates)
+    int nseg, nband, band_rows;
+};
+
+struct FwdArgs : Geometry {
+    const void* img;
+    int64_t img_pitch;  // elements
+    void* out;
+    int64_t out_pitch;  // elements
+    const float* kappa;
+    const float* wx;
+    const float* wy;
+    int aligned;  // image rows can be staged with 16 / 8-byte copies
+    int out_vec;  // output rows can be written with 16 / 8-byte stores
+};
+
+// The backward pass always covers every image pixel (its output is d img, H x W), so its
+// Geometry is the full image; the cotangent grad_out sits at (oy, ox) inside it with size
+// (gho, gwo) (VALID: offset 2 and size (H-4, W-4); CLAMP: offset 0 and size (H, W)).
+struct BwdArgs : Geometry {
+    const void* img;
+    int64_t img_pitch;
+    const void* gout;
+    int64_t gout_pitch;
+    int gho, gwo;
+    void* gimg;        // nullable
+    int64_t gimg_pitch;
+    const float* kappa;
+    const float* wx;
+    const float* wy;
+    double* partials;  // [kParamSlots][nseg * nband]
+    int aligned;       // image staging
+    int g_aligned;     // cotangent staging (CLAMP with aligned pointer and pitch)
+    int gimg_vec;      // d img rows can be written with 16 / 8-byte stores
+    void* rout;        // fused forward output R (nullable; storage type of the image)
+    int64_t rout_pitch;
+    int rout_vec;      // R rows can be written with 16 / 8-byte stores
+};
+
+cudaError_t launch_harris_fwd(const FwdArgs& a, int dt, int out_dt, cudaStream_t s);
+cudaError_t launch_harris_bwd(const BwdArgs& a, int dt, int gout_dt, cudaStream_t s);
+// out[f] = sum over n partials[f * n + i] (fixed order, float64), f < kParamSlots; any out
+// pointer may be NULL.
+cudaError_t launch_finalize_params(const double* partials, int64_t n, float* gkappa, float* gwx,
+                                   float* gwy, cudaStream_t s);
+
+}  // namespace shine

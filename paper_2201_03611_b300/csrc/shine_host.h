@@ -1,0 +1,27 @@
+// Host-side helpers shared by the entry points (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "harris_kernels.h"
+#include "shine.h"
+
+namespace shine {
+
+constexpr int64_t kMaxDim = int64_t(1) << 30;
+constexpr int kFwdWarpsPerSm = 32;  // target warps per SM when choosing band heights
+constexpr int kBwdWarpsPerSm = 16;
+
+shine_status cuda_status(cudaError_t e);
+size_t dtype_size(int dt);
+bool dtype_ok(int dt);
+bool border_ok(int b);
+int sm_count();
+shine_status check_shape(int64_t H, int64_t W, int border);
+bool aligned_to(const void* p, size_t a);
+void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows);
+Geometry fwd_geometry(int64_t H, int64_t W, int border, int band_rows_override);
+Geometry bwd_geometry(int64_t H, int64_t W, int border, int band_rows_override);
+
+}  // namespace shine

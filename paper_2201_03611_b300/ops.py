@@ -1,0 +1,197 @@
+"""Torch-facing calls of the fused Harris pipeline (device memory and streams from torch;
+every computation in libshine's CUDA kernels).
+
+Images are (H, W, 3) CUDA tensors with channel stride 1 and pixel stride 3 (any row stride
+>= 3W); response maps and cotangents are (H_out, W_out) with column stride 1. kappa is a
+CUDA float32 tensor with one element; wx, wy are (3, 3) CUDA float32 tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: L.SHINE_F32, torch.bfloat16: L.SHINE_BF16, torch.float16: L.SHINE_F16}
+_BORDER = {"valid": L.SHINE_VALID, "clamp": L.SHINE_CLAMP}
+
+
+def dtype_code(dt: torch.dtype) -> int:
+    if dt not in _DT:
+        raise TypeError(f"unsupported storage dtype {dt}; use float32, bfloat16 or float16")
+    return _DT[dt]
+
+
+def border_code(border: str) -> int:
+    if border not in _BORDER:
+        raise ValueError(f"border must be 'valid' or 'clamp', not {border!r}")
+    return _BORDER[border]
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(dev: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _check_img(img: torch.Tensor) -> None:
+    if not img.is_cuda or img.dim() != 3 or img.shape[2] != 3:
+        raise ValueError("img must be a CUDA tensor of shape (H, W, 3)")
+    if img.stride(2) != 1 or img.stride(1) != 3:
+        raise ValueError("img must have channel stride 1 and pixel stride 3 (rows may be padded)")
+
+
+def _check_map(t: torch.Tensor, shape, name: str) -> None:
+    if not t.is_cuda or tuple(t.shape) != tuple(shape) or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise ValueError(f"{name} must be a CUDA tensor of shape {tuple(shape)} with column stride 1")
+
+
+def _param(t, name: str, numel: int) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() \
+            or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor with {numel} elements")
+    return t
+
+
+def output_shape(h: int, w: int, border: str) -> tuple[int, int]:
+    ho, wo = ctypes.c_int64(), ctypes.c_int64()
+    L.check(L.lib().shine_output_shape(h, w, border_code(border), ctypes.byref(ho), ctypes.byref(wo)),
+            "shine_output_shape")
+    return ho.value, wo.value
+
+
+def bwd_workspace_bytes(h: int, w: int, border: str) -> int:
+    n = ctypes.c_size_t()
+    L.check(L.lib().shine_pipeline_bwd_workspace(h, w, border_code(border), ctypes.byref(n)),
+            "shine_pipeline_bwd_workspace")
+    return n.value
+
+
+def _row_pitch(t: torch.Tensor) -> int:
+    return t.stride(0)
+
+
+def pipeline_fwd(img, kappa, wx, wy, border: str = "clamp", out_dtype=None, out=None) -> torch.Tensor:
+    """R = fused Harris response (shine_pipeline_fwd)."""
+    _check_img(img)
+    _param(kappa, "kappa", 1); _param(wx, "wx", 9); _param(wy, "wy", 9)
+    h, w = img.shape[0], img.shape[1]
+    ho, wo = output_shape(h, w, border)
+    odt = img.dtype if out_dtype is None else out_dtype
+    if out is None:
+        out = torch.empty(ho, wo, device=img.device, dtype=odt)
+    _check_map(out, (ho, wo), "out")
+    L.check(L.lib().shine_pipeline_fwd(_ptr(img), h, w, _row_pitch(img), dtype_code(img.dtype), border_code(border),
+                                       _ptr(kappa), _ptr(wx), _ptr(wy), _ptr(out), _row_pitch(out),
+                                       dtype_code(out.dtype), _stream(img.device)), "shine_pipeline_fwd")
+    return out
+
+
+def _grads_out(img, need_img, need_params, grad_img=None):
+    dev = img.device
+    gimg = grad_img if grad_img is not None else (torch.empty_like(img) if need_img else None)
+    gk = torch.empty(1, device=dev, dtype=torch.float32) if need_params else None
+    gwx = torch.empty(3, 3, device=dev, dtype=torch.float32) if need_params else None
+    gwy = torch.empty(3, 3, device=dev, dtype=torch.float32) if need_params else None
+    return gimg, gk, gwx, gwy
+
+
+def pipeline_bwd(img, grad_out, kappa, wx, wy, border: str = "clamp", need_img: bool = True,
+                 need_params: bool = True, workspace=None, grad_img=None):
+    """(d img, d kappa, d wx, d wy) of L = sum(grad_out * R) (shine_pipeline_bwd)."""
+    _check_img(img)
+    _param(kappa, "kappa", 1); _param(wx, "wx", 9); _param(wy, "wy", 9)
+    h, w = img.shape[0], img.shape[1]
+    ho, wo = output_shape(h, w, border)
+    _check_map(grad_out, (ho, wo), "grad_out")
+    gimg, gk, gwx, gwy = _grads_out(img, need_img, need_params, grad_img)
+    if gimg is not None:
+        _check_img(gimg)
+    nbytes = bwd_workspace_bytes(h, w, border)
+    if workspace is None:
+        workspace = torch.empty(max(nbytes, 16), device=img.device, dtype=torch.uint8)
+    L.check(L.lib().shine_pipeline_bwd(_ptr(img), h, w, _row_pitch(img), dtype_code(img.dtype), border_code(border),
+                                       _ptr(kappa), _ptr(wx), _ptr(wy), _ptr(grad_out), _row_pitch(grad_out),
+                                       dtype_code(grad_out.dtype), _ptr(gimg),
+                                       _row_pitch(gimg) if gimg is not None else 0, _ptr(gk), _ptr(gwx), _ptr(gwy),
+                                       _ptr(workspace), workspace.numel(), _stream(img.device)),
+            "shine_pipeline_bwd")
+    return gimg, gk, gwx, gwy
+
+
+def pipeline_fwd_bwd(img, grad_out, kappa, wx, wy, border: str = "clamp", need_img: bool = True,
+                     need_params: bool = True, workspace=None, out=None, grad_img=None):
+    """(R, d img, d kappa, d wx, d wy) in one pass (shine_pipeline_fwd_bwd)."""
+    _check_img(img)
+    _param(kappa, "kappa", 1); _param(wx, "wx", 9); _param(wy, "wy", 9)
+    h, w = img.shape[0], img.shape[1]
+    ho, wo = output_shape(h, w, border)
+    _check_map(grad_out, (ho, wo), "grad_out")
+    if grad_out.dtype != img.dtype:
+        raise TypeError("shine_pipeline_fwd_bwd takes grad_out in the image's storage dtype")
+    if out is None:
+        out = torch.empty(ho, wo, device=img.device, dtype=img.dtype)
+    _check_map(out, (ho, wo), "out")
+    gimg, gk, gwx, gwy = _grads_out(img, need_img, need_params, grad_img)
+    nbytes = bwd_workspace_bytes(h, w, border)
+    if workspace is None:
+        workspace = torch.empty(max(nbytes, 16), device=img.device, dtype=torch.uint8)
+    L.check(L.lib().shine_pipeline_fwd_bwd(_ptr(img), h, w, _row_pitch(img), dtype_code(img.dtype),
+                                           border_code(border), _ptr(kappa), _ptr(wx), _ptr(wy), _ptr(grad_out),
+                                           _row_pitch(grad_out), _ptr(out), _row_pitch(out), _ptr(gimg),
+                                           _row_pitch(gimg) if gimg is not None else 0, _ptr(gk), _ptr(gwx),
+                                           _ptr(gwy), _ptr(workspace), workspace.numel(), _stream(img.device)),
+            "shine_pipeline_fwd_bwd")
+    return out, gimg, gk, gwx, gwy
+
+
+def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
+    if isinstance(v, torch.Tensor):
+        return v
+    return torch.full(shape, float(v), device=like.device, dtype=torch.float32)
+
+
+class HarrisFn(torch.autograd.Function):
+    """R = harris(img, kappa, wx, wy) with the hand-written adjoint kernel as its backward.
+
+    Gradients are returned for img (storage dtype), kappa, wx and wy (float32). The Sobel
+    stage is recomputed in the backward kernel; only the inputs are saved."""
+
+    @staticmethod
+    def forward(ctx, img, kappa, wx, wy, border="clamp", out_dtype=None):
+        kappa_c = kappa.reshape(1).contiguous()
+        out = pipeline_fwd(img, kappa_c, wx.contiguous(), wy.contiguous(), border, out_dtype)
+        ctx.save_for_backward(img, kappa_c, wx, wy)
+        ctx.border = border
+        ctx.kappa_shape = kappa.shape
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        img, kappa, wx, wy = ctx.saved_tensors
+        need_img = ctx.needs_input_grad[0]
+        need_params = any(ctx.needs_input_grad[1:4])
+        if not (need_img or need_params):
+            return None, None, None, None, None, None
+        if grad_out.dtype not in (img.dtype, torch.float32):
+            grad_out = grad_out.float()
+        grad_out = grad_out.contiguous()  # autograd may hand over an expanded (stride 0) tensor
+        gimg, gk, gwx, gwy = pipeline_bwd(img, grad_out, kappa, wx.contiguous(), wy.contiguous(), ctx.border,
+                                          need_img=need_img, need_params=need_params)
+        return (gimg if need_img else None,
+                gk.reshape(ctx.kappa_shape) if ctx.needs_input_grad[1] else None,
+                gwx if ctx.needs_input_grad[2] else None,
+                gwy if ctx.needs_input_grad[3] else None, None, None)
+
+
+def harris(img, kappa=0.04, wx=None, wy=None, border: str = "clamp", out_dtype=None) -> torch.Tensor:
+    """Differentiable Harris response of an (H, W, 3) CUDA image (default Sobel weights)."""
+    if wx is None or wy is None:
+        sx = torch.tensor([[-1.0, 0.0, 1.0], [-2.0, 0.0, 2.0], [-1.0, 0.0, 1.0]], device=img.device)
+        wx = sx if wx is None else wx
+        wy = sx.t().contiguous() if wy is None else wy
+    kappa = _as_param(kappa, img, (1,))
+    return HarrisFn.apply(img, kappa, wx, wy, border, out_dtype)

@@ -1,0 +1,139 @@
+"""The persistent batched path: per-image parity with the single-image fused entry and with the
+oracle, CUDA-graph capture and replay, and the tuning cache."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import gpu_util as U
+import workloads as wl
+from oracle import cref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def shine():
+    import paper_2201_03611_b300 as S
+    return S
+
+
+def _batch(n, dtype, seed, lo=5, hi=300, border="clamp"):
+    b = wl.batch_512(n=n, dtype=dtype, seed=seed, lo=lo, hi=hi)
+    imgs = [t.cuda() for t in b["imgs"]]
+    ws = [t.cuda() for t in b["ws"]]
+    if border == "valid":
+        ws = [w[: w.shape[0] - 4, : w.shape[1] - 4].contiguous() for w in ws]
+    return b, imgs, ws
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("border", ["clamp", "valid"])
+def test_batched_equals_per_image(shine, dtype, border):
+    b, imgs, ws = _batch(14, dtype, seed=3, border=border)
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    plan = shine.BatchedPlan(shapes, imgs[0].dtype, border, fwd_bwd=True)
+    outs = [torch.empty(shine.output_shape(h, w, border), dtype=imgs[0].dtype, device="cuda") for h, w in shapes]
+    gimgs = [torch.empty_like(t) for t in imgs]
+    descs = plan.bind(imgs, outs, ws, gimgs)
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.random_weights(4)]
+    gk = torch.empty(len(imgs), device="cuda")
+    gwx = torch.empty(3, 3, device="cuda")
+    gwy = torch.empty(3, 3, device="cuda")
+    plan.run(descs, kappa, wx, wy, gk, gwx, gwy)
+    torch.cuda.synchronize()
+    swx = torch.zeros(3, 3, device="cuda")
+    swy = torch.zeros(3, 3, device="cuda")
+    for i, img in enumerate(imgs):
+        r, gi, k1, wx1, wy1 = shine.pipeline_fwd_bwd(img, ws[i], kappa[i:i + 1].contiguous(), wx, wy, border)
+        assert torch.equal(outs[i], r), i          # same per-pixel arithmetic, whatever the tiling
+        assert torch.equal(gimgs[i], gi), i
+        assert U.rel(U.host(gk[i:i + 1]), U.host(k1)) <= 1e-6
+        swx += wx1
+        swy += wy1
+    assert U.rel(U.host(gwx), U.host(swx)) <= 1e-5
+    assert U.rel(U.host(gwy), U.host(swy)) <= 1e-5
+
+
+def test_batched_against_oracle(shine):
+    b, imgs, ws = _batch(6, "bf16", seed=5, lo=5, hi=200)
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True)
+    outs = [torch.empty(h, w, dtype=torch.bfloat16, device="cuda") for h, w in shapes]
+    gimgs = [torch.empty_like(t) for t in imgs]
+    descs = plan.bind(imgs, outs, ws, gimgs)
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.sobel_weights()]
+    gk = torch.empty(len(imgs), device="cuda")
+    gwx, gwy = torch.empty(3, 3, device="cuda"), torch.empty(3, 3, device="cuda")
+    plan.run(descs, kappa, wx, wy, gk, gwx, gwy)
+    torch.cuda.synchronize()
+    swx, swy = np.zeros((3, 3)), np.zeros((3, 3))
+    for i in range(len(imgs)):
+        ki = float(b["kappa"][i])
+        ref = cref.forward(b["imgs"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp")
+        assert U.rel(U.host(outs[i]), ref) <= U.TOL_16
+        gi, gki, gwxi, gwyi = cref.backward(b["imgs"][i], b["ws"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp")
+        assert U.rel(U.host(gimgs[i]), gi) <= U.TOL_16
+        assert U.rel(U.host(gk[i:i + 1]), [gki]) <= U.TOL_PARAM
+        swx += gwxi
+        swy += gwyi
+    assert U.rel(U.host(gwx), swx) <= U.TOL_PARAM
+    assert U.rel(U.host(gwy), swy) <= U.TOL_PARAM
+
+
+def test_batched_forward_only(shine):
+    b, imgs, _ = _batch(9, "f32", seed=7)
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    plan = shine.BatchedPlan(shapes, torch.float32, "clamp", fwd_bwd=False)
+    outs = [torch.empty(h, w, device="cuda") for h, w in shapes]
+    descs = plan.bind(imgs, outs)
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.sobel_weights()]
+    plan.run(descs, kappa, wx, wy)
+    torch.cuda.synchronize()
+    for i, img in enumerate(imgs):
+        r = shine.pipeline_fwd(img, kappa[i:i + 1].contiguous(), wx, wy, "clamp")
+        assert torch.equal(outs[i], r)
+
+
+def test_graph_capture_and_replay(shine):
+    b, imgs, ws = _batch(10, "bf16", seed=11)
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True)
+    outs = [torch.empty(h, w, dtype=torch.bfloat16, device="cuda") for h, w in shapes]
+    gimgs = [torch.empty_like(t) for t in imgs]
+    descs = plan.bind(imgs, outs, ws, gimgs)
+    ws_buf = plan.new_workspace("cuda")
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.sobel_weights()]
+    gk = torch.empty(len(imgs), device="cuda")
+    gwx, gwy = torch.empty(3, 3, device="cuda"), torch.empty(3, 3, device="cuda")
+    plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws_buf)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in outs + gimgs + [gk, gwx, gwy]]
+    for t in outs + gimgs + [gk, gwx, gwy]:
+        t.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws_buf)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(eager, outs + gimgs + [gk, gwx, gwy]):
+        assert torch.equal(x, y)
+
+
+def test_tune_cache_is_honoured(shine, tmp_path):
+    from paper_2201_03611_b300.tune import gpu_key
+    shapes = [(100, 90), (1000, 40), (33, 33)]
+    path = tmp_path / "tune.txt"
+    # bucket of 100 rows is 7 (2^7 = 128 >= 100), of 1000 rows 10, of 33 rows 6
+    path.write_text(f"# test\n{gpu_key()} 1 1 3 7 24\n{gpu_key()} 1 1 3 10 200\n")
+    plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=str(path))
+    assert [plan.tile_rows(i) for i in range(3)] == [24, 200, 33]

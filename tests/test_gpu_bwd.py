@@ -1,0 +1,173 @@
+"""Adjoint kernel parity: against the oracle's FP64 reverse-mode gradient element by element,
+against FP64 finite differences on a 32x32 crop, determinism, the fused forward+backward
+entry, and the torch.autograd.Function."""
+import numpy as np
+import pytest
+import torch
+
+import gpu_util as U
+import workloads as wl
+from oracle import cref
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [((1, 1), "clamp"), ((1, 6), "clamp"), ((2, 2), "clamp"), ((4, 3), "clamp"), ((7, 129), "clamp"),
+          ((37, 250), "clamp"), ((130, 367), "clamp"), ((301, 9), "clamp"), ((64, 124), "clamp"),
+          ((5, 5), "valid"), ((9, 133), "valid"), ((70, 245), "valid")]
+
+
+@pytest.fixture(scope="module")
+def shine():
+    import paper_2201_03611_b300 as S
+    return S
+
+
+def _run_bwd(shine, img, g, kappa, wx, wy, border, **kw):
+    k, dwx, dwy = U.dev_params(kappa, wx, wy)
+    return shine.pipeline_bwd(img.cuda(), g.cuda(), k, dwx, dwy, border, **kw)
+
+
+@pytest.mark.parametrize("shape,border", SHAPES)
+def test_bwd_f32_matches_oracle(shine, shape, border):
+    h, w = shape
+    img = wl.random_image(h, w, seed=h * 7 + w)
+    wx, wy = wl.random_weights(h)
+    ho, wo = shine.output_shape(h, w, border)
+    g = wl.random_cotangent(ho, wo, seed=w)
+    gi, gk, gwx, gwy = cref.backward(img, g, 0.05, wx, wy, border)
+    dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, 0.05, wx, wy, border)
+    torch.cuda.synchronize()
+    assert U.rel(U.host(dgi), gi) <= U.TOL_GIMG
+    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM
+    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
+    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+
+
+def test_fd_on_32x32_crop(shine):
+    """The differentiation workload's check: FP64 central differences of the oracle on the
+    top-left 32x32 crop (as a CLAMP image of its own) for all 3072 + 1 + 18 parameters."""
+    cfg = wl.diff_2048()
+    img = cfg["img"][:32, :32].contiguous()
+    g = cfg["w"][:32, :32].contiguous()
+    wx, wy = wl.sobel_weights()
+    kappa = cfg["kappa"]
+    img64, g64 = img.double(), g.double().numpy()
+
+    def L(im=img64, k=kappa, a=wx.double(), b=wy.double()):
+        return float(np.sum(g64 * cref.forward(im, k, a, b, "clamp")))
+    fd_img = np.zeros((32, 32, 3))
+    for i in range(32):
+        for j in range(32):
+            for c in range(3):
+                hh = 1e-6 * max(1.0, abs(float(img64[i, j, c])))
+                p, m = img64.clone(), img64.clone()
+                p[i, j, c] += hh
+                m[i, j, c] -= hh
+                fd_img[i, j, c] = (L(im=p) - L(im=m)) / (2 * hh)
+    hk = 1e-6 * max(1.0, kappa)
+    fd_k = (L(k=kappa + hk) - L(k=kappa - hk)) / (2 * hk)
+    fd_w = []
+    for which in (0, 1):
+        out = np.zeros((3, 3))
+        base = (wx if which == 0 else wy).double()
+        for a in range(3):
+            for b in range(3):
+                hh = 1e-6 * max(1.0, abs(float(base[a, b])))
+                p, m = base.clone(), base.clone()
+                p[a, b] += hh
+                m[a, b] -= hh
+                out[a, b] = ((L(a=p) - L(a=m)) if which == 0 else (L(b=p) - L(b=m))) / (2 * hh)
+        fd_w.append(out)
+    dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, kappa, wx, wy, "clamp")
+    assert U.rel(U.host(dgi), fd_img) <= U.TOL_FD
+    assert U.rel(U.host(dgk), [fd_k]) <= U.TOL_FD
+    assert U.rel(U.host(dgwx), fd_w[0]) <= U.TOL_FD
+    assert U.rel(U.host(dgwy), fd_w[1]) <= U.TOL_FD
+
+
+def test_diff_2048_full(shine):
+    """The 2048 x 2048 differentiation workload against the oracle's full FP64 gradient."""
+    cfg = wl.diff_2048()
+    wx, wy = wl.sobel_weights()
+    gi, gk, gwx, gwy = cref.backward(cfg["img"], cfg["w"], cfg["kappa"], wx, wy, "clamp")
+    dgi, dgk, dgwx, dgwy = _run_bwd(shine, cfg["img"], cfg["w"], cfg["kappa"], wx, wy, "clamp")
+    assert U.rel(U.host(dgi), gi) <= U.TOL_GIMG
+    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM
+    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
+    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_bwd_16bit_storage(shine, dtype):
+    img = wl.random_image(130, 367, seed=3, dtype=dtype)
+    g = wl.random_cotangent(130, 367, seed=4, dtype=dtype)
+    wx, wy = wl.sobel_weights()
+    gi, gk, gwx, gwy = cref.backward(img, g, 0.04, wx, wy, "clamp")    # oracle on quantised inputs
+    dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, 0.04, wx, wy, "clamp")
+    assert dgi.dtype == img.dtype
+    assert U.rel(U.host(dgi), gi) <= U.TOL_16
+    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM                      # float32 accumulation
+    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
+    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+    # float32 cotangent with a 16-bit image
+    dgi32 = _run_bwd(shine, img, g.float(), 0.04, wx, wy, "clamp")[0]
+    assert U.rel(U.host(dgi32), gi) <= U.TOL_16
+
+
+def test_bwd_deterministic(shine):
+    img = wl.random_image(300, 500, seed=5)
+    g = wl.random_cotangent(300, 500, seed=6)
+    wx, wy = wl.random_weights(5)
+    a = _run_bwd(shine, img, g, 0.04, wx, wy, "clamp")
+    b = _run_bwd(shine, img, g, 0.04, wx, wy, "clamp")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("shape,border", [((37, 250), "clamp"), ((70, 245), "valid"), ((3, 3), "clamp")])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fused_equals_separate(shine, shape, border, dtype):
+    h, w = shape
+    img = wl.random_image(h, w, seed=8).to(dtype).cuda()
+    ho, wo = shine.output_shape(h, w, border)
+    g = wl.random_cotangent(ho, wo, seed=9).to(dtype).cuda()
+    k, dwx, dwy = U.dev_params(0.04, *wl.random_weights(8))
+    r = shine.pipeline_fwd(img, k, dwx, dwy, border)
+    sep = shine.pipeline_bwd(img, g, k, dwx, dwy, border)
+    fused = shine.pipeline_fwd_bwd(img, g, k, dwx, dwy, border)
+    assert torch.equal(fused[0], r)
+    for x, y in zip(fused[1:], sep):
+        assert torch.equal(x, y)
+
+
+def test_bwd_unaligned_paths_bit_identical(shine):
+    img = wl.random_image(41, 250, seed=10).cuda()
+    g = wl.random_cotangent(41, 250, seed=11).cuda()
+    k, dwx, dwy = U.dev_params(0.04, *wl.random_weights(10))
+    a = shine.pipeline_bwd(img, g, k, dwx, dwy, "clamp")
+    gstore = torch.zeros(41, 251, device="cuda")
+    gstore[:, 1:] = g
+    b = shine.pipeline_bwd(U.padded_image(img, 1), gstore[:, 1:], k, dwx, dwy, "clamp")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_autograd_function(shine):
+    img = wl.random_image(45, 140, seed=12).cuda().requires_grad_(True)
+    wx, wy = wl.random_weights(12)
+    k = torch.tensor([0.05], device="cuda", requires_grad=True)
+    wxd = wx.cuda().requires_grad_(True)
+    wyd = wy.cuda().requires_grad_(True)
+    g = wl.random_cotangent(45, 140, seed=13).cuda()
+    r = shine.harris(img, k, wxd, wyd, "clamp")
+    (r * g).sum().backward()
+    gi, gk, gwx, gwy = cref.backward(img.detach().cpu(), g.cpu(), 0.05, wx, wy, "clamp")
+    assert U.rel(U.host(img.grad), gi) <= U.TOL_GIMG
+    assert U.rel(U.host(k.grad), [gk]) <= U.TOL_PARAM
+    assert U.rel(U.host(wxd.grad), gwx) <= U.TOL_PARAM
+    assert U.rel(U.host(wyd.grad), gwy) <= U.TOL_PARAM
+    # sum() hands an expanded cotangent to backward
+    img2 = img.detach().clone().requires_grad_(True)
+    shine.harris(img2, 0.05, wxd.detach(), wyd.detach(), "valid").sum().backward()
+    gi2 = cref.backward(img.detach().cpu(), torch.ones(41, 136), 0.05, wx, wy, "valid")[0]
+    assert U.rel(U.host(img2.grad), gi2) <= U.TOL_GIMG
