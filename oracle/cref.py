@@ -40,7 +40,7 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         p, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         L.oracle_harris_forward.argtypes = [p, i64, i64, i, d, p, p, p, i]
-        L.oracle_harris_backward.argtypes = [p, p, i64, i64, i, d, p, p, p, p, p, p, i]
+        L.oracle_harris_backward.argtypes = [p, p, i64, i64, i, d, p, p, p, p, p, p, p, i]
         L.oracle_harris_forward_points.argtypes = [p, i64, i64, i, d, p, p, p, i64, p, i]
         L.oracle_harris_backward_points.argtypes = [p, p, i64, i64, i, d, p, p, p, i64, p, i]
         L.oracle_harris_param_grads.argtypes = [p, p, i64, i64, i, d, p, p, p, p, p, i]
@@ -85,8 +85,11 @@ def forward(img, kappa, wx, wy, border, nthreads: int = 0) -> np.ndarray:
     return out
 
 
-def backward(img, g, kappa, wx, wy, border, nthreads: int = 0):
-    """(d img [H,W,3], d kappa, d Wx [3,3], d Wy [3,3]) in FP64 for L = sum(g * R)."""
+def backward(img, g, kappa, wx, wy, border, nthreads: int = 0, with_abs: bool = False):
+    """(d img [H,W,3], d kappa, d Wx [3,3], d Wy [3,3]) in FP64 for L = sum(g * R).
+
+    with_abs: also return the sum of |term| of each parameter cotangent's sum, as
+    (abs kappa, abs Wx [3,3], abs Wy [3,3])."""
     x, gg = _f64(img), _f64(g)
     h, w = x.shape[0], x.shape[1]
     b = _BORDERS[border]
@@ -96,10 +99,14 @@ def backward(img, g, kappa, wx, wy, border, nthreads: int = 0):
     gk = np.zeros(1, np.float64)
     gwx, gwy = np.zeros(9, np.float64), np.zeros(9, np.float64)
     wxd, wyd = _f64(wx).reshape(9), _f64(wy).reshape(9)
+    absp = np.zeros(19, np.float64)
     _check(lib().oracle_harris_backward(_ptr(x), _ptr(gg), h, w, b, float(kappa), _ptr(wxd),
                                         _ptr(wyd), _ptr(gimg), _ptr(gk), _ptr(gwx), _ptr(gwy),
-                                        nthreads), "backward")
-    return gimg, float(gk[0]), gwx.reshape(3, 3), gwy.reshape(3, 3)
+                                        _ptr(absp), nthreads), "backward")
+    out = (gimg, float(gk[0]), gwx.reshape(3, 3), gwy.reshape(3, 3))
+    if with_abs:
+        return out + ((float(absp[0]), absp[1:10].reshape(3, 3), absp[10:19].reshape(3, 3)),)
+    return out
 
 
 def forward_points(img, kappa, wx, wy, border, pts, nthreads: int = 0) -> np.ndarray:

@@ -23,6 +23,7 @@
  * and all outputs are double. Images are H x W x 3, row-major, channel fastest, dense.
  * Return value: 0 on success, -1 on a bad argument, -2 when memory runs out.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -62,11 +63,12 @@ static void stencil3(const double* x, int64_t h, int64_t w, int clamp, const dou
         }
 }
 
-/* Adjoint of stencil3: gx += scatter of wt*gy, gwt += sum gy * x (gwt may be NULL). */
+/* Adjoint of stencil3: gx += scatter of wt*gy, gwt += sum gy * x (gwt may be NULL), and
+ * gabs += sum |gy * x|, the magnitude of the terms of that sum (gabs may be NULL). */
 static void stencil3_vjp(const double* x, int64_t h, int64_t w, int clamp, const double* wt,
-                         const double* gy, double* gx, double* gwt) {
+                         const double* gy, double* gx, double* gwt, double* gabs) {
     int64_t ho = clamp ? h : h - 2, wo = clamp ? w : w - 2;
-    double gw[9] = {0};
+    double gw[9] = {0}, ga[9] = {0};
     for (int64_t i = 0; i < ho; ++i)
         for (int64_t j = 0; j < wo; ++j) {
             double g = gy[i * wo + j];
@@ -75,10 +77,13 @@ static void stencil3_vjp(const double* x, int64_t h, int64_t w, int clamp, const
                     int64_t k = tap(i, a, h, clamp) * w + tap(j, b, w, clamp);
                     gx[k] += wt[a * 3 + b] * g;
                     gw[a * 3 + b] += g * x[k];
+                    ga[a * 3 + b] += fabs(g * x[k]);
                 }
         }
     if (gwt)
         for (int t = 0; t < 9; ++t) gwt[t] += gw[t];
+    if (gabs)
+        for (int t = 0; t < 9; ++t) gabs[t] += ga[t];
 }
 
 typedef struct {
@@ -155,10 +160,12 @@ int oracle_harris_forward(const double* img, int64_t H, int64_t W, int border, d
     return 0;
 }
 
-/* Cotangents of L = sum(g * R): gimg (H x W x 3), gkappa[1], gwx[9], gwy[9]. g is h2 x w2. */
+/* Cotangents of L = sum(g * R): gimg (H x W x 3), gkappa[1], gwx[9], gwy[9]. g is h2 x w2.
+ * absp (nullable, 19 entries: kappa, Wx, Wy) receives the sum of |term| of each parameter
+ * cotangent's sum, the scale against which a floating-point evaluation of it is judged. */
 int oracle_harris_backward(const double* img, const double* g, int64_t H, int64_t W, int border,
                            double kappa, const double* wx, const double* wy, double* gimg,
-                           double* gkappa, double* gwx, double* gwy, int nthreads) {
+                           double* gkappa, double* gwx, double* gwy, double* absp, int nthreads) {
     if (!img || !g || !wx || !wy || !gimg || !gkappa || !gwx || !gwy || check_args(H, W, border))
         return -1;
     set_threads(nthreads);
@@ -175,19 +182,23 @@ int oracle_harris_backward(const double* img, const double* g, int64_t H, int64_
         goto done;
     }
     /* A5 adjoint; kappa is shared by every pixel, so its cotangent is the sum. */
-    double gk = 0.0;
+    double gk = 0.0, gk_abs = 0.0;
     for (size_t k = 0; k < n2; ++k) {
         double tr = s.Sxx[k] + s.Syy[k], gv = g[k];
         gSxx[k] = gv * (s.Syy[k] - 2.0 * kappa * tr);
         gSyy[k] = gv * (s.Sxx[k] - 2.0 * kappa * tr);
         gSxy[k] = -2.0 * gv * s.Sxy[k];
         gk += -gv * tr * tr;
+        gk_abs += fabs(gv * tr * tr);
     }
     *gkappa = gk;
+    if (absp)
+        for (int t = 0; t < 19; ++t) absp[t] = 0.0;
+    if (absp) absp[0] = gk_abs;
     /* A4 adjoint. */
-    stencil3_vjp(s.Pxx, s.h1, s.w1, clamp, kOnes, gSxx, gPxx, NULL);
-    stencil3_vjp(s.Pxy, s.h1, s.w1, clamp, kOnes, gSxy, gPxy, NULL);
-    stencil3_vjp(s.Pyy, s.h1, s.w1, clamp, kOnes, gSyy, gPyy, NULL);
+    stencil3_vjp(s.Pxx, s.h1, s.w1, clamp, kOnes, gSxx, gPxx, NULL, NULL);
+    stencil3_vjp(s.Pxy, s.h1, s.w1, clamp, kOnes, gSxy, gPxy, NULL, NULL);
+    stencil3_vjp(s.Pyy, s.h1, s.w1, clamp, kOnes, gSyy, gPyy, NULL, NULL);
     /* A3 adjoint. */
     for (size_t k = 0; k < n1; ++k) {
         gIx[k] = 2.0 * s.Ix[k] * gPxx[k] + s.Iy[k] * gPxy[k];
@@ -195,8 +206,8 @@ int oracle_harris_backward(const double* img, const double* g, int64_t H, int64_
     }
     /* A2 adjoint. */
     for (int t = 0; t < 9; ++t) { gwx[t] = 0.0; gwy[t] = 0.0; }
-    stencil3_vjp(s.G, H, W, clamp, wx, gIx, gG, gwx);
-    stencil3_vjp(s.G, H, W, clamp, wy, gIy, gG, gwy);
+    stencil3_vjp(s.G, H, W, clamp, wx, gIx, gG, gwx, absp ? absp + 1 : NULL);
+    stencil3_vjp(s.G, H, W, clamp, wy, gIy, gG, gwy, absp ? absp + 10 : NULL);
     /* A1 adjoint. */
     for (size_t k = 0; k < n0; ++k)
         for (int c = 0; c < 3; ++c) gimg[k * 3 + c] = kGray[c] * gG[k];

@@ -3,6 +3,7 @@
 // memory except shine_plan_create (in batched.cu), and nothing synchronises.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -39,16 +40,6 @@ shine_status check_shape(int64_t H, int64_t W, int border) {
     return SHINE_OK;
 }
 
-int choose_band_rows(int64_t rows, int64_t nseg, int64_t target_warps, int min_rows) {
-    if (rows <= 0) return 1;
-    int64_t nband = (target_warps + nseg - 1) / nseg;
-    if (nband < 1) nband = 1;
-    int64_t br = (rows + nband - 1) / nband;
-    if (br < min_rows) br = min_rows;
-    if (br > rows) br = rows;
-    return (int)br;
-}
-
 void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows) {
     g.H = (int)H;
     g.W = (int)W;
@@ -63,26 +54,24 @@ void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_imag
     g.nseg = (g.xhi + kSegOut - 1) / kSegOut;
     g.band_rows = band_rows;
     g.nband = (g.yhi - g.ylo + band_rows - 1) / band_rows;
+    g.nwarps = 0;
 }
 
-Geometry fwd_geometry(int64_t H, int64_t W, int border, int band_rows_override) {
+Geometry fwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
-    fill_geometry(g, H, W, border, false, 1);
-    const int64_t rows = g.yhi - g.ylo;
-    const int br = band_rows_override > 0 ? band_rows_override
-                                          : choose_band_rows(rows, g.nseg, (int64_t)sm_count() * kFwdWarpsPerSm, 16);
-    fill_geometry(g, H, W, border, false, br);
+    fill_geometry(g, H, W, border, false, (int)H);
     return g;
 }
 
-Geometry bwd_geometry(int64_t H, int64_t W, int border, int band_rows_override) {
+Geometry bwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
-    fill_geometry(g, H, W, border, true, 1);
-    const int64_t rows = g.yhi - g.ylo;
-    const int br = band_rows_override > 0 ? band_rows_override
-                                          : choose_band_rows(rows, g.nseg, (int64_t)sm_count() * kBwdWarpsPerSm, 32);
-    fill_geometry(g, H, W, border, true, br);
+    fill_geometry(g, H, W, border, true, (int)H);
     return g;
+}
+
+int64_t bwd_max_warps(const Geometry& g) {
+    const int64_t units = (int64_t)(g.yhi - g.ylo) * g.nseg;
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * kMaxWarpsPerSm, units / kBwdMinRows));
 }
 
 bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -132,7 +121,7 @@ shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t i
         !aligned_to(wy, 4))
         return SHINE_ERR_ALIGNMENT;
     FwdArgs a;
-    static_cast<Geometry&>(a) = fwd_geometry(H, W, border, 0);
+    static_cast<Geometry&>(a) = fwd_geometry(H, W, border);
     a.img = img; a.img_pitch = img_pitch; a.out = out; a.out_pitch = out_pitch;
     a.kappa = kappa; a.wx = wx; a.wy = wy;
     const size_t chunk = si == 4 ? 16 : 8;
@@ -145,8 +134,8 @@ shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border bor
     if (!bytes) return SHINE_ERR_INVALID_ARG;
     shine_status st = check_shape(H, W, border);
     if (st != SHINE_OK) return st;
-    Geometry g = bwd_geometry(H, W, border, 0);
-    *bytes = (size_t)kParamSlots * (size_t)g.nseg * (size_t)g.nband * sizeof(double);
+    Geometry g = bwd_geometry(H, W, border);
+    *bytes = (size_t)kParamSlots * (size_t)bwd_max_warps(g) * sizeof(double);
     return SHINE_OK;
 }
 
@@ -174,8 +163,9 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
         (grad_wy && !aligned_to(grad_wy, 4)))
         return SHINE_ERR_ALIGNMENT;
     BwdArgs a;
-    static_cast<Geometry&>(a) = bwd_geometry(H, W, border, 0);
-    const size_t need = (size_t)kParamSlots * (size_t)a.nseg * (size_t)a.nband * sizeof(double);
+    static_cast<Geometry&>(a) = bwd_geometry(H, W, border);
+    const int64_t max_warps = bwd_max_warps(a);
+    const size_t need = (size_t)kParamSlots * (size_t)max_warps * sizeof(double);
     if (!workspace || ws_bytes < need) return SHINE_ERR_WORKSPACE;
     if (!aligned_to(workspace, 16)) return SHINE_ERR_ALIGNMENT;
     if (!out && !grad_img && !grad_kappa && !grad_wx && !grad_wy) return SHINE_OK;
@@ -191,10 +181,11 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     a.rout = out; a.rout_pitch = out_pitch;
     a.rout_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * si) && ((size_t)out_pitch * si) % (4 * si) == 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    st = cuda_status(launch_harris_bwd(a, dt, gout_dt, s));
+    int used = 0;
+    st = cuda_status(launch_harris_bwd(a, dt, gout_dt, (int)max_warps, s, &used));
     if (st != SHINE_OK) return st;
     if (grad_kappa || grad_wx || grad_wy)
-        st = cuda_status(launch_finalize_params(a.partials, (int64_t)a.nseg * a.nband, grad_kappa, grad_wx, grad_wy, s));
+        st = cuda_status(launch_finalize_params(a.partials, used, grad_kappa, grad_wx, grad_wy, s));
     return st;
 }
 

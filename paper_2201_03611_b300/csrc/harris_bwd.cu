@@ -22,6 +22,8 @@
 // one per stencil, forward and adjoint). Lanes 0 and 31 supply exactly the 4-column halo.
 // Parameter cotangents are accumulated per lane in float32, reduced per warp in float64 and
 // summed in a fixed order by the finalize kernel, so every run gives the same bits.
+#include <algorithm>
+
 #include "harris_bwd_strip.cuh"
 
 namespace shine {
@@ -34,14 +36,7 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kBwdThreads / 32) + warp;
-    const int nwarps = a.nseg * a.nband;
-    if (gw >= nwarps) return;  // whole warp
-    const int seg = gw % a.nseg;
-    const int band = gw / a.nseg;
-    const int xb = a.x0 + seg * kSegOut;
-    const int x = xb - 4 + 4 * lane;
-    const int y0 = a.ylo + band * a.band_rows;
-    const int y1 = min(y0 + a.band_rows, a.yhi);
+    if (gw >= a.nwarps) return;  // whole warp
     const int tid = warp * 32 + lane;
     TI* ring = reinterpret_cast<TI*>(smem_raw) + tid * NS * 12;
     TG* gring = reinterpret_cast<TG*>(smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI)) + tid * NS * 4;
@@ -50,14 +45,26 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
     float acc[kParamSlots];
 #pragma unroll
     for (int i = 0; i < kParamSlots; ++i) acc[i] = 0.0f;
-    const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W);
     TI* rout = static_cast<TI*>(a.rout);
-    if (edge)
-        bwd_strip<TI, TG, NS, true, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
-                                                               a.rout_pitch, a.rout_vec);
-    else
-        bwd_strip<TI, TG, NS, false, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, y0, y1, ring, gring, acc, rout,
-                                                                a.rout_pitch, a.rout_vec);
+    // This warp's equal share of the (segment, row) units, walked segment by segment.
+    const int64_t rows = a.yhi - a.ylo;
+    int64_t lo, hi;
+    balanced_slice(rows * a.nseg, a.nwarps, gw, lo, hi);
+    while (lo < hi) {
+        const int seg = (int)(lo / rows);
+        const int r0 = (int)(lo % rows);
+        const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
+        const int xb = a.x0 + seg * kSegOut;
+        const int x = xb - 4 + 4 * lane;
+        const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W);
+        if (edge)
+            bwd_strip<TI, TG, NS, true, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
+                                                                   gring, acc, rout, a.rout_pitch, a.rout_vec);
+        else
+            bwd_strip<TI, TG, NS, false, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
+                                                                    gring, acc, rout, a.rout_pitch, a.rout_vec);
+        lo += r1 - r0;
+    }
     // Warp partials in float64, lanes 0 and 31 excluded by selection (their values may be
     // unrelated to this warp's pixels).
     const bool producer = lane >= 1 && lane <= 30;
@@ -66,28 +73,42 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
         double v = producer ? (double)acc[i] : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (lane == 0) a.partials[(int64_t)i * nwarps + gw] = v;
+        if (lane == 0) a.partials[(int64_t)i * a.nwarps + gw] = v;
     }
 }
 
+template <typename K>
+int resident_warps(K kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    return per_sm * sms * (threads / 32);
+}
+
 template <typename TI, typename TG>
-cudaError_t launch_bwd_t(const BwdArgs& a, cudaStream_t s) {
+cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
     constexpr int NS = kBwdStages;
-    const int64_t warps = (int64_t)a.nseg * a.nband;
-    const int64_t blocks = (warps + kBwdThreads / 32 - 1) / (kBwdThreads / 32);
     const size_t smem = (size_t)kBwdThreads * NS * (12 * sizeof(TI) + 4 * sizeof(TG));
-    if (blocks <= 0) return cudaSuccess;
-#define SHINE_BWD_LAUNCH(AL, GA, WR) \
-    harris_bwd_kernel<TI, TG, NS, AL, GA, WR><<<(unsigned)blocks, kBwdThreads, smem, s>>>(a)
     const bool wr = a.rout != nullptr;
-    if (a.aligned && a.g_aligned) {
-        if (wr) SHINE_BWD_LAUNCH(true, true, true); else SHINE_BWD_LAUNCH(true, true, false);
-    } else if (a.aligned) {
-        if (wr) SHINE_BWD_LAUNCH(true, false, true); else SHINE_BWD_LAUNCH(true, false, false);
-    } else {
-        if (wr) SHINE_BWD_LAUNCH(false, false, true); else SHINE_BWD_LAUNCH(false, false, false);
-    }
-#undef SHINE_BWD_LAUNCH
+    void (*kern)(BwdArgs);
+    if (a.aligned && a.g_aligned)
+        kern = wr ? harris_bwd_kernel<TI, TG, NS, true, true, true> : harris_bwd_kernel<TI, TG, NS, true, true, false>;
+    else if (a.aligned)
+        kern = wr ? harris_bwd_kernel<TI, TG, NS, true, false, true> : harris_bwd_kernel<TI, TG, NS, true, false, false>;
+    else
+        kern = wr ? harris_bwd_kernel<TI, TG, NS, false, false, true>
+                  : harris_bwd_kernel<TI, TG, NS, false, false, false>;
+    const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
+    int64_t t = resident_warps(kern, kBwdThreads, smem);
+    t = std::min<int64_t>(t, std::max<int64_t>(1, units / kBwdMinRows));
+    t = std::max<int64_t>(1, std::min<int64_t>(t, max_warps));
+    a.nwarps = (int)t;
+    if (used) *used = a.nwarps;
+    const int64_t blocks = (t + kBwdThreads / 32 - 1) / (kBwdThreads / 32);
+    kern<<<(unsigned)blocks, kBwdThreads, smem, s>>>(a);
     return cudaPeekAtLastError();
 }
 
@@ -114,9 +135,9 @@ __global__ void __launch_bounds__(256) finalize_params_kernel(const double* part
 
 }  // namespace
 
-cudaError_t launch_harris_bwd(const BwdArgs& a, int dt, int gout_dt, cudaStream_t s) {
+cudaError_t launch_harris_bwd(BwdArgs a, int dt, int gout_dt, int max_warps, cudaStream_t s, int* used) {
 #define SHINE_BWD_CASE(I, G, TI, TG) \
-    if (dt == I && gout_dt == G) return launch_bwd_t<TI, TG>(a, s);
+    if (dt == I && gout_dt == G) return launch_bwd_t<TI, TG>(a, max_warps, s, used);
     SHINE_BWD_CASE(0, 0, float, float)
     SHINE_BWD_CASE(1, 1, __nv_bfloat16, __nv_bfloat16)
     SHINE_BWD_CASE(2, 2, __half, __half)

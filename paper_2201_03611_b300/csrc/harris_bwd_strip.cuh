@@ -145,6 +145,13 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     TI* gimg = static_cast<TI*>(a.gimg);
     const float kc[3] = {kGrayR, kGrayG, kGrayB};
+    // Two-level sum of the parameter cotangents: `part` collects kFlushRows rows, then is added
+    // into `acc`, so no float32 accumulator sees more than ~4 * max(kFlushRows, rows/kFlushRows)
+    // terms.
+    constexpr int kFlushRows = 16;
+    float part[kParamSlots];
+#pragma unroll
+    for (int i = 0; i < kParamSlots; ++i) part[i] = 0.0f;
 
 #pragma unroll 1
     for (int s = 2; s < nrows; ++s) {
@@ -215,7 +222,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 gsn[1][j] = -2.0f * g * sxy;
                 gsn[2][j] = g * (sxx - k2);
                 float dk = -g * tr * tr;
-                acc[0] += (own_row && cin[j]) ? dk : 0.0f;
+                part[0] += (own_row && cin[j]) ? dk : 0.0f;
             }
         }
         // B3: gP at row k = r-3 = clamped box sum of gS rows k-1, k, k+1.
@@ -261,12 +268,12 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 float ex = own ? gIx[j] : 0.0f, ey = own ? gIy[j] : 0.0f;
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    acc[1 + b] = fmaf(ex, G0[j + b], acc[1 + b]);
-                    acc[4 + b] = fmaf(ex, G1[j + b], acc[4 + b]);
-                    acc[7 + b] = fmaf(ex, G2[j + b], acc[7 + b]);
-                    acc[10 + b] = fmaf(ey, G0[j + b], acc[10 + b]);
-                    acc[13 + b] = fmaf(ey, G1[j + b], acc[13 + b]);
-                    acc[16 + b] = fmaf(ey, G2[j + b], acc[16 + b]);
+                    part[1 + b] = fmaf(ex, G0[j + b], part[1 + b]);
+                    part[4 + b] = fmaf(ex, G1[j + b], part[4 + b]);
+                    part[7 + b] = fmaf(ex, G2[j + b], part[7 + b]);
+                    part[10 + b] = fmaf(ey, G0[j + b], part[10 + b]);
+                    part[13 + b] = fmaf(ey, G1[j + b], part[13 + b]);
+                    part[16 + b] = fmaf(ey, G2[j + b], part[16 + b]);
                 }
             }
         }
@@ -354,12 +361,18 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 }
             }
         }
+        if ((s & (kFlushRows - 1)) == 0) {
+#pragma unroll
+            for (int i = 0; i < kParamSlots; ++i) { acc[i] += part[i]; part[i] = 0.0f; }
+        }
         // shift the windows
         copy4(ix0, ix1); copy4(iy0, iy1); copy4(ix1, ix2); copy4(iy1, iy2);
 #pragma unroll
         for (int q = 0; q < 3; ++q) { copy4(gs0[q], gs1[q]); copy4(gs1[q], gsn[q]); }
         copy6(gx0, gx1); copy6(gy0, gy1); copy6(gx1, gxn); copy6(gy1, gyn);
     }
+#pragma unroll
+    for (int i = 0; i < kParamSlots; ++i) acc[i] += part[i];
     cp_async_wait<0>();
 }
 

@@ -25,8 +25,17 @@ struct Geometry {
     int ylo, yhi;      // output rows, in image coordinates: [ylo, yhi)
     int ox, oy;        // image coordinates of output element (0, 0)
     int x0;            // first output column of segment 0 (image coordinates)
-    int nseg, nband, band_rows;
+    int nseg;          // column segments of kSegOut output columns
+    int nband, band_rows;  // row bands (tile lists of the batched path)
+    int nwarps;        // single-image kernels: warps sharing the nseg x rows work units
 };
+
+// Balanced split of n work units over t workers: worker w gets [lo, hi), sizes differ by <= 1.
+__host__ __device__ inline void balanced_slice(int64_t n, int64_t t, int64_t w, int64_t& lo, int64_t& hi) {
+    const int64_t q = n / t, rem = n % t;
+    lo = q * w + (w < rem ? w : rem);
+    hi = lo + q + (w < rem ? 1 : 0);
+}
 
 struct FwdArgs : Geometry {
     const void* img;
@@ -63,8 +72,14 @@ struct BwdArgs : Geometry {
     int rout_vec;      // R rows can be written with 16 / 8-byte stores
 };
 
-cudaError_t launch_harris_fwd(const FwdArgs& a, int dt, int out_dt, cudaStream_t s);
-cudaError_t launch_harris_bwd(const BwdArgs& a, int dt, int gout_dt, cudaStream_t s);
+// The launchers choose a.nwarps: one resident wave (occupancy x SMs), at most max_warps, and
+// no more than leaves each warp min_rows rows. The backward's partials need
+// kParamSlots x a.nwarps doubles; *nwarps_used (nullable) reports the count.
+cudaError_t launch_harris_fwd(FwdArgs a, int dt, int out_dt, cudaStream_t s);
+cudaError_t launch_harris_bwd(BwdArgs a, int dt, int gout_dt, int max_warps, cudaStream_t s, int* nwarps_used);
+constexpr int kFwdMinRows = 16;  // minimum rows per warp slice
+constexpr int kBwdMinRows = 32;
+constexpr int kMaxWarpsPerSm = 64;
 // out[f] = sum over n partials[f * n + i] (fixed order, float64), f < kParamSlots; any out
 // pointer may be NULL.
 cudaError_t launch_finalize_params(const double* partials, int64_t n, float* gkappa, float* gwx,

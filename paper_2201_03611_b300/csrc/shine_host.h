@@ -10,8 +10,6 @@
 namespace shine {
 
 constexpr int64_t kMaxDim = int64_t(1) << 30;
-constexpr int kFwdWarpsPerSm = 32;  // target warps per SM when choosing band heights
-constexpr int kBwdWarpsPerSm = 16;
 
 shine_status cuda_status(cudaError_t e);
 size_t dtype_size(int dt);
@@ -21,7 +19,9 @@ int sm_count();
 shine_status check_shape(int64_t H, int64_t W, int border);
 bool aligned_to(const void* p, size_t a);
 void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows);
-Geometry fwd_geometry(int64_t H, int64_t W, int border, int band_rows_override);
-Geometry bwd_geometry(int64_t H, int64_t W, int border, int band_rows_override);
+Geometry fwd_geometry(int64_t H, int64_t W, int border);
+Geometry bwd_geometry(int64_t H, int64_t W, int border);
+// Upper bound of the warps a backward launch uses (its partials need kParamSlots doubles each).
+int64_t bwd_max_warps(const Geometry& g);
 
 }  // namespace shine

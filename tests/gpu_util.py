@@ -6,13 +6,18 @@ import torch
 # ill-posed where R cancels to ~0):
 #   float32 storage, against the FP64 oracle ............................ 1e-5
 #   bf16 / fp16 storage, against the oracle run on the quantised input .. 2e-2
-#   float32 gradients against the oracle's FP64 reverse-mode gradient ... 1e-5 for d img,
-#                                         1e-4 for the summed parameter cotangents
+#   float32 d img against the oracle's FP64 reverse-mode gradient ....... 1e-5
 #   float32 gradients against FP64 finite differences on a 32x32 crop ... 1e-4
+#   summed parameter cotangents (d kappa, d Wx, d Wy): |got - ref| <= 2e-5 * sum |term|.
+#     A sum of n floating-point terms is only determined to a multiple of eps * sum |term|
+#     (the standard summation error bound); measuring its error relative to |sum| instead
+#     is ill-conditioned wherever the terms cancel (g ~ N(0,1) makes them cancel). The
+#     kernel's error budget: float32 terms (relative error ~1e-6 from the float32 pipeline)
+#     plus a two-level float32 sum per lane (<= ~64 eps) and float64 above the lane.
 TOL_F32 = 1e-5
 TOL_16 = 2e-2
 TOL_GIMG = 1e-5
-TOL_PARAM = 1e-4
+TOL_PARAM_COND = 2e-5
 TOL_FD = 1e-4
 
 
@@ -37,3 +42,22 @@ def padded_image(img: torch.Tensor, extra: int) -> torch.Tensor:
     store = torch.zeros(h, 3 * w + extra, dtype=img.dtype, device=img.device)
     store[:, :3 * w] = img.reshape(h, 3 * w)
     return store.as_strided((h, w, 3), (3 * w + extra, 3, 1))
+
+
+def param_errors(got, ref_abs) -> dict:
+    """Condition-aware errors of (d kappa, d Wx, d Wy): got = device tensors, ref_abs = the
+    oracle's (value, value, value, (abs, abs, abs)) from cref.backward(..., with_abs=True)[1:]."""
+    gk, gwx, gwy = got
+    rk, rwx, rwy, (ak, awx, awy) = ref_abs
+    out = {}
+    for name, g, r, a in (("kappa", gk, [rk], [ak]), ("wx", gwx, rwx, awx), ("wy", gwy, rwy, awy)):
+        g = host(g).reshape(-1)
+        r = np.asarray(r, np.float64).reshape(-1)
+        a = np.asarray(a, np.float64).reshape(-1)
+        out[name] = float(np.max(np.abs(g - r) / np.maximum(a, 1e-300)))
+    return out
+
+
+def assert_params(got, ref_abs, tol=TOL_PARAM_COND):
+    errs = param_errors(got, ref_abs)
+    assert all(v <= tol for v in errs.values()), errs

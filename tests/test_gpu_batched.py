@@ -44,17 +44,22 @@ def test_batched_equals_per_image(shine, dtype, border):
     gwy = torch.empty(3, 3, device="cuda")
     plan.run(descs, kappa, wx, wy, gk, gwx, gwy)
     torch.cuda.synchronize()
-    swx = torch.zeros(3, 3, device="cuda")
-    swy = torch.zeros(3, 3, device="cuda")
+    awx, awy = np.zeros((3, 3)), np.zeros((3, 3))
+    swx, swy = np.zeros((3, 3)), np.zeros((3, 3))
     for i, img in enumerate(imgs):
         r, gi, k1, wx1, wy1 = shine.pipeline_fwd_bwd(img, ws[i], kappa[i:i + 1].contiguous(), wx, wy, border)
         assert torch.equal(outs[i], r), i          # same per-pixel arithmetic, whatever the tiling
         assert torch.equal(gimgs[i], gi), i
-        assert U.rel(U.host(gk[i:i + 1]), U.host(k1)) <= 1e-6
-        swx += wx1
-        swy += wy1
-    assert U.rel(U.host(gwx), U.host(swx)) <= 1e-5
-    assert U.rel(U.host(gwy), U.host(swy)) <= 1e-5
+        # both are float32 per-lane sums over differently banded rows: compare each with the
+        # oracle on the summation scale sum |term|
+        ref = cref.backward(img.cpu(), ws[i].cpu(), float(kappa[i]), wx.cpu(), wy.cpu(), border, with_abs=True)
+        U.assert_params((gk[i:i + 1], wx1, wy1), ref[1:])
+        U.assert_params((k1, wx1, wy1), ref[1:])
+        swx += ref[2]
+        swy += ref[3]
+        awx += ref[4][1]
+        awy += ref[4][2]
+    U.assert_params((gk[:1], gwx, gwy), (float(U.host(gk[:1])[0]), swx, swy, (1.0, awx, awy)))
 
 
 def test_batched_against_oracle(shine):
@@ -71,17 +76,20 @@ def test_batched_against_oracle(shine):
     plan.run(descs, kappa, wx, wy, gk, gwx, gwy)
     torch.cuda.synchronize()
     swx, swy = np.zeros((3, 3)), np.zeros((3, 3))
+    awx, awy = np.zeros((3, 3)), np.zeros((3, 3))
     for i in range(len(imgs)):
         ki = float(b["kappa"][i])
         ref = cref.forward(b["imgs"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp")
         assert U.rel(U.host(outs[i]), ref) <= U.TOL_16
-        gi, gki, gwxi, gwyi = cref.backward(b["imgs"][i], b["ws"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp")
+        gi, gki, gwxi, gwyi, absi = cref.backward(b["imgs"][i], b["ws"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp",
+                                                  with_abs=True)
         assert U.rel(U.host(gimgs[i]), gi) <= U.TOL_16
-        assert U.rel(U.host(gk[i:i + 1]), [gki]) <= U.TOL_PARAM
+        U.assert_params((gk[i:i + 1], gwx, gwy), (gki, U.host(gwx), U.host(gwy), (absi[0], 1.0, 1.0)))
         swx += gwxi
         swy += gwyi
-    assert U.rel(U.host(gwx), swx) <= U.TOL_PARAM
-    assert U.rel(U.host(gwy), swy) <= U.TOL_PARAM
+        awx += absi[1]
+        awy += absi[2]
+    U.assert_params((gk[:1], gwx, gwy), (float(U.host(gk[:1])[0]), swx, swy, (1.0, awx, awy)))
 
 
 def test_batched_forward_only(shine):

@@ -34,13 +34,11 @@ def test_bwd_f32_matches_oracle(shine, shape, border):
     wx, wy = wl.random_weights(h)
     ho, wo = shine.output_shape(h, w, border)
     g = wl.random_cotangent(ho, wo, seed=w)
-    gi, gk, gwx, gwy = cref.backward(img, g, 0.05, wx, wy, border)
+    ref = cref.backward(img, g, 0.05, wx, wy, border, with_abs=True)
     dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, 0.05, wx, wy, border)
     torch.cuda.synchronize()
-    assert U.rel(U.host(dgi), gi) <= U.TOL_GIMG
-    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM
-    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
-    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+    assert U.rel(U.host(dgi), ref[0]) <= U.TOL_GIMG
+    U.assert_params((dgk, dgwx, dgwy), ref[1:])
 
 
 def test_fd_on_32x32_crop(shine):
@@ -89,12 +87,10 @@ def test_diff_2048_full(shine):
     """The 2048 x 2048 differentiation workload against the oracle's full FP64 gradient."""
     cfg = wl.diff_2048()
     wx, wy = wl.sobel_weights()
-    gi, gk, gwx, gwy = cref.backward(cfg["img"], cfg["w"], cfg["kappa"], wx, wy, "clamp")
+    ref = cref.backward(cfg["img"], cfg["w"], cfg["kappa"], wx, wy, "clamp", with_abs=True)
     dgi, dgk, dgwx, dgwy = _run_bwd(shine, cfg["img"], cfg["w"], cfg["kappa"], wx, wy, "clamp")
-    assert U.rel(U.host(dgi), gi) <= U.TOL_GIMG
-    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM
-    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
-    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+    assert U.rel(U.host(dgi), ref[0]) <= U.TOL_GIMG
+    U.assert_params((dgk, dgwx, dgwy), ref[1:])
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
@@ -102,16 +98,14 @@ def test_bwd_16bit_storage(shine, dtype):
     img = wl.random_image(130, 367, seed=3, dtype=dtype)
     g = wl.random_cotangent(130, 367, seed=4, dtype=dtype)
     wx, wy = wl.sobel_weights()
-    gi, gk, gwx, gwy = cref.backward(img, g, 0.04, wx, wy, "clamp")    # oracle on quantised inputs
+    ref = cref.backward(img, g, 0.04, wx, wy, "clamp", with_abs=True)  # oracle on quantised inputs
     dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, 0.04, wx, wy, "clamp")
     assert dgi.dtype == img.dtype
-    assert U.rel(U.host(dgi), gi) <= U.TOL_16
-    assert U.rel(U.host(dgk), [gk]) <= U.TOL_PARAM                      # float32 accumulation
-    assert U.rel(U.host(dgwx), gwx) <= U.TOL_PARAM
-    assert U.rel(U.host(dgwy), gwy) <= U.TOL_PARAM
+    assert U.rel(U.host(dgi), ref[0]) <= U.TOL_16
+    U.assert_params((dgk, dgwx, dgwy), ref[1:])                          # float32 arithmetic
     # float32 cotangent with a 16-bit image
     dgi32 = _run_bwd(shine, img, g.float(), 0.04, wx, wy, "clamp")[0]
-    assert U.rel(U.host(dgi32), gi) <= U.TOL_16
+    assert U.rel(U.host(dgi32), ref[0]) <= U.TOL_16
 
 
 def test_bwd_deterministic(shine):
@@ -161,11 +155,9 @@ def test_autograd_function(shine):
     g = wl.random_cotangent(45, 140, seed=13).cuda()
     r = shine.harris(img, k, wxd, wyd, "clamp")
     (r * g).sum().backward()
-    gi, gk, gwx, gwy = cref.backward(img.detach().cpu(), g.cpu(), 0.05, wx, wy, "clamp")
-    assert U.rel(U.host(img.grad), gi) <= U.TOL_GIMG
-    assert U.rel(U.host(k.grad), [gk]) <= U.TOL_PARAM
-    assert U.rel(U.host(wxd.grad), gwx) <= U.TOL_PARAM
-    assert U.rel(U.host(wyd.grad), gwy) <= U.TOL_PARAM
+    ref = cref.backward(img.detach().cpu(), g.cpu(), 0.05, wx, wy, "clamp", with_abs=True)
+    assert U.rel(U.host(img.grad), ref[0]) <= U.TOL_GIMG
+    U.assert_params((k.grad, wxd.grad, wyd.grad), ref[1:])
     # sum() hands an expanded cotangent to backward
     img2 = img.detach().clone().requires_grad_(True)
     shine.harris(img2, 0.05, wxd.detach(), wyd.detach(), "valid").sum().backward()
