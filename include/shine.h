@@ -123,6 +123,29 @@ SHINE_API shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W,
                                 float* grad_wy, void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Backward pass that allocates nothing, for callers that cannot allocate device memory (a
+ * plug-in handed only its input and output buffers, a real-time loop that forbids allocation
+ * after start-up, code inside a framework that owns all device memory). The paper has no
+ * counterpart; this is an interface convenience of this library.
+ *
+ * Same arguments and results as shine_pipeline_bwd, without the workspace: the per-warp partial
+ * sums live in one fixed array of the library's device memory (about 2.5 MB: 19 x 16384
+ * doubles), held on every GPU that loads the library until the process exits. Returns
+ * SHINE_ERR_UNSUPPORTED when an image would need more partial sums than that array holds (not
+ * reached on GPUs with up to 256 SMs). The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call before any stream
+ * capture. All calls share the one array: calls whose GPU work can overlap in time (different
+ * streams without ordering between them, or several host threads) race on it and give wrong
+ * cotangents; serialise them on one stream. Nothing needs clearing between calls.
+ */
+SHINE_API shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, int64_t W, int64_t img_pitch,
+                                    shine_dtype dt, shine_border border, const float* kappa,
+                                    const float* wx, const float* wy, const void* grad_out,
+                                    int64_t gout_pitch, shine_dtype gout_dt, void* grad_img,
+                                    int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
+                                    float* grad_wy, void* stream);
+
+/*
  * Many images of different sizes in one persistent launch.
  *
  * shine_plan_create builds, on the host and then once on the device, the tile list of a fixed
