@@ -44,7 +44,7 @@ namespace shine {
 namespace {
 
 constexpr int kBatchThreads = 128;
-constexpr int kBatchStages = 4;
+template <bool FWD_BWD> constexpr int batch_stages() { return FWD_BWD ? kBwdStages : kFwdStages; }
 
 struct BatchArgs {
     const shine_image_desc* descs;
@@ -80,12 +80,12 @@ __device__ __forceinline__ bool dev_aligned(const void* p, int64_t pitch, size_t
 template <typename T, bool FWD_BWD>
 __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int NS = kBatchStages;
+    constexpr int NS = batch_stages<FWD_BWD>();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int tid = warp * 32 + lane;
-    T* ring = reinterpret_cast<T*>(smem_raw) + tid * NS * 12;
-    T* gring = reinterpret_cast<T*>(smem_raw + (size_t)kBatchThreads * NS * 12 * sizeof(T)) + tid * NS * 4;
+    T* ring = reinterpret_cast<T*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
+    T* gring = reinterpret_cast<T*>(smem_raw + (size_t)kBatchThreads * NS * 12 * sizeof(T)) +
+               warp * NS * kLanes * 4 + lane * 4;
     constexpr size_t chunk = sizeof(T) == 4 ? 16 : 8;
     const bool producer = lane >= 1 && lane <= 30;
     Params P;
@@ -186,11 +186,13 @@ __global__ void __launch_bounds__(256) finalize_batched_kernel(const double* par
 
 template <typename T, bool FWD_BWD>
 size_t batched_smem() {
-    return (size_t)kBatchThreads * kBatchStages * (12 + (FWD_BWD ? 4 : 0)) * sizeof(T);
+    return (size_t)kBatchThreads * batch_stages<FWD_BWD>() * (12 + (FWD_BWD ? 4 : 0)) * sizeof(T);
 }
 
 template <typename T, bool FWD_BWD>
 int batched_grid() {
+    cudaFuncSetAttribute(harris_batched_kernel<T, FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batched_smem<T, FWD_BWD>());
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harris_batched_kernel<T, FWD_BWD>, kBatchThreads,
                                                       batched_smem<T, FWD_BWD>()) != cudaSuccess ||
@@ -201,6 +203,9 @@ int batched_grid() {
 
 template <typename T, bool FWD_BWD>
 cudaError_t launch_batched_t(const BatchArgs& b, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(harris_batched_kernel<T, FWD_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem<T, FWD_BWD>());
+    if (e != cudaSuccess) return e;
     harris_batched_kernel<T, FWD_BWD><<<grid, kBatchThreads, batched_smem<T, FWD_BWD>(), s>>>(b);
     return cudaPeekAtLastError();
 }

@@ -37,9 +37,9 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kBwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
-    const int tid = warp * 32 + lane;
-    TI* ring = reinterpret_cast<TI*>(smem_raw) + tid * NS * 12;
-    TG* gring = reinterpret_cast<TG*>(smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI)) + tid * NS * 4;
+    TI* ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
+    TG* gring = reinterpret_cast<TG*>(smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI)) +
+                warp * NS * kLanes * 4 + lane * 4;
     Params P;
     load_params(P, a.wx, a.wy, a.kappa);
     float acc[kParamSlots];
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
     // This warp's equal share of the (segment, row) units, walked segment by segment.
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    balanced_slice(rows * a.nseg, a.nwarps, gw, lo, hi);
+    warp_work(SHINE_BWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
     while (lo < hi) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
@@ -102,6 +102,8 @@ cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
         kern = wr ? harris_bwd_kernel<TI, TG, NS, false, false, true>
                   : harris_bwd_kernel<TI, TG, NS, false, false, false>;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int64_t t = resident_warps(kern, kBwdThreads, smem);
     t = std::min<int64_t>(t, std::max<int64_t>(1, units / kBwdMinRows));
     t = std::max<int64_t>(1, std::min<int64_t>(t, max_warps));

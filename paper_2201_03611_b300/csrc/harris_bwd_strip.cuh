@@ -7,11 +7,13 @@
 
 namespace shine {
 
-// The lane's 4 cotangent values of successive rows (one 16- or 8-byte chunk per row).
+// The lane's 4 cotangent values of successive rows (one 16- or 8-byte chunk per row), staged
+// like the image rows: a slot holds the 32 lanes' chunks side by side.
 template <typename T, int NS, bool EDGE, bool ALIGNED>
 struct CotRows {
     static constexpr int kChunk = 4 * sizeof(T);
-    T* ring;
+    static constexpr int kSlot = kLanes * 4;
+    T* ring;  // this lane's 4 elements of slot 0
     const T* g;
     int64_t pitch;
     int x, ox, oy, gho, gwo;
@@ -34,7 +36,7 @@ struct CotRows {
             const char* src = nb > 0
                 ? reinterpret_cast<const char*>(g + (int64_t)gy * pitch + (x - ox))
                 : reinterpret_cast<const char*>(g);
-            uint32_t dst = smem_u32(ring + slot * 4);
+            uint32_t dst = smem_u32(ring + slot * kSlot);
             if constexpr (kChunk == 16) cp_async16(dst, src, nb);
             else cp_async8(dst, src, nb);
         }
@@ -43,10 +45,10 @@ struct CotRows {
     __device__ __forceinline__ void read(int slot, int r, float v[4]) const {
         if constexpr (ALIGNED) {
             if constexpr (sizeof(T) == 4) {
-                float4 q = *reinterpret_cast<const float4*>(ring + slot * 4);
+                float4 q = *reinterpret_cast<const float4*>(ring + slot * kSlot);
                 v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
             } else {
-                uint2 q = *reinterpret_cast<const uint2*>(ring + slot * 4);
+                uint2 q = *reinterpret_cast<const uint2*>(ring + slot * kSlot);
                 v[0] = Bits16<T>::to_f(q.x & 0xffffu);
                 v[1] = Bits16<T>::to_f(q.x >> 16);
                 v[2] = Bits16<T>::to_f(q.y & 0xffffu);
@@ -64,17 +66,11 @@ struct CotRows {
     }
 };
 
-__device__ __forceinline__ void copy6(float d[6], const float s[6]) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) d[i] = s[i];
-}
-__device__ __forceinline__ void copy4(float d[4], const float s[4]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = s[i];
-}
-
 // WITH_R: also store R (computed anyway in B1) into rout at the rows this warp owns, for the
 // fused forward+backward pass; rout has the output geometry of the forward pass.
+//
+// acc receives this strip's parameter cotangents: acc[0] = d kappa, acc[1 + t] = d Wx[t],
+// acc[10 + t] = d Wy[t] (t = 3a + b), for the rows [y0, y1) and producer columns it owns.
 template <typename TI, typename TG, int NS, bool EDGE, bool ALIGNED, bool GALIGNED, bool WITH_R = false>
 __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int lane, int x, int y0,
                                           int y1, TI* ring, TG* gring, float acc[kParamSlots],
@@ -124,201 +120,193 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     // Register windows (row index relative to the lead image row r of the current step).
     float G0[6], G1[6], G2[6], G3[6], G4[6];  // gray rows r-4 .. r
-    float ix0[4], iy0[4], ix1[4], iy1[4];       // I rows r-3, r-2 (r-1 computed per step)
-    float gs0[3][4], gs1[3][4];                 // gS rows r-4, r-3 (r-2 computed per step)
-    float gx0[6], gy0[6], gx1[6], gy1[6];       // gI0 rows r-5, r-4 (6 wide)
+    float2 I0[4], I1[4];                       // (Ix, Iy) rows r-3, r-2 (r-1 computed per step)
+    float2 gs0[4], gs1[4];                     // (gSxx, gSyy) rows r-4, r-3 (r-2 per step)
+    float gq0[4], gq1[4];                      // gSxy rows r-4, r-3
+    float2 gi0[6], gi1[6];                     // (gIx, gIy), zero outside the image, rows r-5, r-4
     float gv[4];
 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        gx0[i] = gy0[i] = gx1[i] = gy1[i] = 0.0f;
+        gi0[i] = gi1[i] = make_float2(0.0f, 0.0f);
         G0[i] = G1[i] = G2[i] = 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        ix0[j] = iy0[j] = ix1[j] = iy1[j] = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) gs0[q][j] = gs1[q][j] = 0.0f;
+        I0[j] = I1[j] = gs0[j] = gs1[j] = make_float2(0.0f, 0.0f);
+        gq0[j] = gq1[j] = 0.0f;
     }
     stage_in(0, G3, gv);  // image rows r_first, r_first + 1; shifted down at every step
     stage_in(1, G4, gv);
 
     TI* gimg = static_cast<TI*>(a.gimg);
     const float kc[3] = {kGrayR, kGrayG, kGrayB};
-    // Two-level sum of the parameter cotangents: `part` collects kFlushRows rows, then is added
-    // into `acc`, so no float32 accumulator sees more than ~4 * max(kFlushRows, rows/kFlushRows)
-    // terms.
+    // Two-level sum of the parameter cotangents: the part* accumulators collect kFlushRows
+    // rows, then are added into acc, so no float32 accumulator sees more than
+    // ~4 * max(kFlushRows, rows / kFlushRows) terms.
     constexpr int kFlushRows = 16;
-    float part[kParamSlots];
+    float2 partw[9];  // (d Wx[t], d Wy[t])
+    float partk = 0.0f;
 #pragma unroll
-    for (int i = 0; i < kParamSlots; ++i) part[i] = 0.0f;
+    for (int i = 0; i < 9; ++i) partw[i] = make_float2(0.0f, 0.0f);
 
-#pragma unroll 1
+#pragma unroll kBwdUnroll
     for (int s = 2; s < nrows; ++s) {
         const int r = r_first + s;
         // shift the gray window down one row and stage row r into G4
-        copy6(G0, G1); copy6(G1, G2); copy6(G2, G3); copy6(G3, G4);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { G0[i] = G1[i]; G1[i] = G2[i]; G2[i] = G3[i]; G3[i] = G4[i]; }
         stage_in(s, G4, gv);
+
         // B1: I at row r-1 (gray rows r-2, r-1, r).
-        float ix2[4], iy2[4];
-        sobel(P, G2, G3, G4, ix2, iy2);
+        float2 I2[4];
+        sobel(P, G2, G3, G4, I2);
 
         // B1: S at row r-2 from products at rows r-3, r-2, r-1 (clamped at their stage).
         const int sr = r - 2;
-        float vs[3][4];
+        float2 v2[4];
+        float vxy[4];
         if (sr == 0 || sr == H - 1) {
-            float ax[4], ay[4], bx[4], by[4];
+            float2 A[4], B[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                ax[j] = (sr == 0) ? ix1[j] : ix0[j];
-                ay[j] = (sr == 0) ? iy1[j] : iy0[j];
-                bx[j] = (sr == H - 1) ? ix1[j] : ix2[j];
-                by[j] = (sr == H - 1) ? iy1[j] : iy2[j];
+                A[j] = (sr == 0) ? I1[j] : I0[j];
+                B[j] = (sr == H - 1) ? I1[j] : I2[j];
             }
-            vertical_products(ax, ay, ix1, iy1, bx, by, vs);
+            vertical_products(A, I1, B, v2, vxy);
         } else {
-            vertical_products(ix0, iy0, ix1, iy1, ix2, iy2, vs);
+            vertical_products(I0, I1, I2, v2, vxy);
         }
-        // B2: gS at row r-2 (horizontal box sum first, then the response adjoint).
-        float gsn[3][4];
-        {
-            float S[3][4];
+        float2 S2[4];  // (Sxx, Syy)
+        float Sxy[4];
+        horizontal_box<EDGE>(v2, S2, x, W);
+        horizontal_box<EDGE>(vxy, Sxy, x, W);
+        const bool own_row = sr >= y0 && sr < y1;
+        if constexpr (WITH_R) {
+            // R at row sr (A5), for rows this warp owns inside the forward output region
+            const int rlo = a.valid ? 2 : 0, rhi = a.valid ? H - 2 : H;
+            if (rout != nullptr && own_row && producer && sr >= rlo && sr < rhi) {
+                float R[4];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) horizontal_box<EDGE>(vs[q], S[q], x, W);
-            const bool own_row = sr >= y0 && sr < y1;
-            if constexpr (WITH_R) {
-                // R at row sr (A5), for rows this warp owns inside the forward output region
-                const int rlo = a.valid ? 2 : 0, rhi = a.valid ? H - 2 : H;
-                if (rout != nullptr && own_row && producer && sr >= rlo && sr < rhi) {
-                    float R[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) R[j] = response(S[0][j], S[1][j], S[2][j], P.kappa);
-                    TI* orow = rout + (int64_t)(sr - rlo) * rpitch;
-                    if (!EDGE && rvec && !a.valid) {
-                        if constexpr (sizeof(TI) == 4) {
-                            *reinterpret_cast<float4*>(orow + x) = make_float4(R[0], R[1], R[2], R[3]);
-                        } else {
-                            TI o[4];
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) o[j] = Conv<TI>::st(R[j]);
-                            *reinterpret_cast<uint2*>(orow + x) = *reinterpret_cast<const uint2*>(o);
-                        }
+                for (int j = 0; j < 4; ++j) R[j] = response(S2[j].x, Sxy[j], S2[j].y, P.kappa);
+                TI* orow = rout + (int64_t)(sr - rlo) * rpitch;
+                if (!EDGE && rvec && !a.valid) {
+                    if constexpr (sizeof(TI) == 4) {
+                        *reinterpret_cast<float4*>(orow + x) = make_float4(R[0], R[1], R[2], R[3]);
                     } else {
+                        TI o[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int c = x + j;
-                            if (c >= rlo && c < W - rlo) orow[c - rlo] = Conv<TI>::st(R[j]);
-                        }
+                        for (int j = 0; j < 4; ++j) o[j] = Conv<TI>::st(R[j]);
+                        *reinterpret_cast<uint2*>(orow + x) = *reinterpret_cast<const uint2*>(o);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = x + j;
+                        if (c >= rlo && c < W - rlo) orow[c - rlo] = Conv<TI>::st(R[j]);
                     }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float sxx = S[0][j], sxy = S[1][j], syy = S[2][j];
-                float tr = sxx + syy;
-                float g = gv[j];
-                float k2 = 2.0f * P.kappa * tr;
-                gsn[0][j] = g * (syy - k2);
-                gsn[1][j] = -2.0f * g * sxy;
-                gsn[2][j] = g * (sxx - k2);
-                float dk = -g * tr * tr;
-                part[0] += (own_row && cin[j]) ? dk : 0.0f;
-            }
         }
+        // B2: gS at row r-2 and the d kappa terms (the cotangent is zero outside the image, so
+        // only the row needs testing; lanes 0 and 31 are dropped when the warp reduces).
+        float2 gsn[4];
+        float gqn[4];
+        float dk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float tr = S2[j].x + S2[j].y;
+            const float g = gv[j];
+            const float k2 = 2.0f * P.kappa * tr;
+            gsn[j] = make_float2(g * (S2[j].y - k2), g * (S2[j].x - k2));
+            gqn[j] = -2.0f * g * Sxy[j];
+            dk[j] = -g * tr * tr;
+        }
+        if (own_row) partk += (dk[0] + dk[1]) + (dk[2] + dk[3]);
         // B3: gP at row k = r-3 = clamped box sum of gS rows k-1, k, k+1.
         const int k = r - 3;
-        float gp[3][4];
+        float2 gp2[4];  // (gPxx, gPyy)
+        float gpq[4];   // gPxy
         {
-            const bool top = k == 0, bot = k == H - 1;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                float vg[4];
+            float2 vg2[4];
+            float vgq[4];
+            if (k == 0 || k == H - 1) {
+                const bool top = k == 0, bot = k == H - 1;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float lo = top ? gs1[q][j] : gs0[q][j];
-                    float hi = bot ? gs1[q][j] : gsn[q][j];
-                    vg[j] = lo + gs1[q][j] + hi;
+                    vg2[j] = __fadd2_rn(__fadd2_rn(top ? gs1[j] : gs0[j], gs1[j]), bot ? gs1[j] : gsn[j]);
+                    vgq[j] = ((top ? gq1[j] : gq0[j]) + gq1[j]) + (bot ? gq1[j] : gqn[j]);
                 }
-                float r6[6];
-                make_row6(vg, r6);
-                if constexpr (EDGE) clamp_row6(r6, x, W);
+            } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) gp[q][j] = r6[j] + r6[j + 1] + r6[j + 2];
+                for (int j = 0; j < 4; ++j) {
+                    vg2[j] = __fadd2_rn(__fadd2_rn(gs0[j], gs1[j]), gsn[j]);
+                    vgq[j] = (gq0[j] + gq1[j]) + gqn[j];
+                }
             }
+            horizontal_box<EDGE>(vg2, gp2, x, W);
+            horizontal_box<EDGE>(vgq, gpq, x, W);
         }
         // B4: gI at row k (zero outside the image: the padded domain of B5).
-        float gIx[4], gIy[4];
-        {
-            const bool row_in = k >= 0 && k < H;
+        float2 gI[4];
+        if (k >= 0 && k < H) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float vx = fmaf(2.0f * ix0[j], gp[0][j], iy0[j] * gp[1][j]);
-                float vy = fmaf(ix0[j], gp[1][j], 2.0f * iy0[j] * gp[2][j]);
-                bool in = row_in && cin[j];
-                gIx[j] = in ? vx : 0.0f;
-                gIy[j] = in ? vy : 0.0f;
+                const float2 i0 = I0[j];
+                float vx = fmaf(2.0f * i0.x, gp2[j].x, i0.y * gpq[j]);
+                float vy = fmaf(i0.x, gpq[j], 2.0f * i0.y * gp2[j].y);
+                gI[j] = make_float2(cin[j] ? vx : 0.0f, cin[j] ? vy : 0.0f);
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gI[j] = make_float2(0.0f, 0.0f);
         }
-        // B5 (weights): d W[a][b] += gI(k, c) * G(clamp(k + a - 1), clamp(c + b - 1)) for the
-        // rows and columns this warp owns. Gray rows k-1, k, k+1 are G0, G1, G2.
-        {
-            const bool own = k >= y0 && k < y1 && producer;
+        // B5 (weights): (d Wx[a][b], d Wy[a][b]) += gI(k, c) * G(clamp(k + a - 1), clamp(c + b - 1))
+        // for the rows this warp owns (gI is zero outside the image; lanes 0 and 31 are dropped
+        // when the warp reduces). Gray rows k-1, k, k+1 are G0, G1, G2.
+        if (k >= y0 && k < y1) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float ex = own ? gIx[j] : 0.0f, ey = own ? gIy[j] : 0.0f;
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    part[1 + b] = fmaf(ex, G0[j + b], part[1 + b]);
-                    part[4 + b] = fmaf(ex, G1[j + b], part[4 + b]);
-                    part[7 + b] = fmaf(ex, G2[j + b], part[7 + b]);
-                    part[10 + b] = fmaf(ey, G0[j + b], part[10 + b]);
-                    part[13 + b] = fmaf(ey, G1[j + b], part[13 + b]);
-                    part[16 + b] = fmaf(ey, G2[j + b], part[16 + b]);
+                    partw[b] = __ffma2_rn(gI[j], dup2(G0[j + b]), partw[b]);
+                    partw[3 + b] = __ffma2_rn(gI[j], dup2(G1[j + b]), partw[3 + b]);
+                    partw[6 + b] = __ffma2_rn(gI[j], dup2(G2[j + b]), partw[6 + b]);
                 }
             }
         }
-        float gxn[6], gyn[6];
-        make_row6(gIx, gxn);
-        make_row6(gIy, gyn);
+        float2 gin[6];
+        make_row6(gI, gin);
 
-        // B5 (image) + B6 at row u = r-4: transposed stencil over gI0 rows u-1 (gx0), u (gx1),
-        // u+1 (gxn), with the vertical clamp folds, then the horizontal folds, then store.
+        // B5 (image) + B6 at row u = r-4: transposed stencil over gI rows u-1 (gi0), u (gi1),
+        // u+1 (gin), with the vertical clamp folds, then the horizontal folds, then store.
         const int u = r - 4;
         if (u >= y0 && gimg != nullptr) {
             float gg[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float t = 0.0f;
+                float2 t = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    const int c = j - b + 2;  // gI0 column v - b + 1 in row6 coordinates
-                    t = fmaf(P.wx[b], gxn[c], t);
-                    t = fmaf(P.wy[b], gyn[c], t);
-                    t = fmaf(P.wx[3 + b], gx1[c], t);
-                    t = fmaf(P.wy[3 + b], gy1[c], t);
-                    t = fmaf(P.wx[6 + b], gx0[c], t);
-                    t = fmaf(P.wy[6 + b], gy0[c], t);
+                    const int c = j - b + 2;  // gI column v - b + 1 in row6 coordinates
+                    t = __ffma2_rn(P.w[b], gin[c], t);
+                    t = __ffma2_rn(P.w[3 + b], gi1[c], t);
+                    t = __ffma2_rn(P.w[6 + b], gi0[c], t);
                 }
-                gg[j] = t;
+                gg[j] = t.x + t.y;
             }
             if (u == 0 || u == H - 1) {
                 // padded row -1 (weights row 0) and row H (weights row 2) fold onto row u
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float t = 0.0f;
+                    float2 t = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const int c = j - b + 2;
-                        if (u == 0) {
-                            t = fmaf(P.wx[b], gx1[c], t);
-                            t = fmaf(P.wy[b], gy1[c], t);
-                        }
-                        if (u == H - 1) {
-                            t = fmaf(P.wx[6 + b], gx1[c], t);
-                            t = fmaf(P.wy[6 + b], gy1[c], t);
-                        }
+                        if (u == 0) t = __ffma2_rn(P.w[b], gi1[c], t);
+                        if (u == H - 1) t = __ffma2_rn(P.w[6 + b], gi1[c], t);
                     }
-                    gg[j] += t;
+                    gg[j] += t.x + t.y;
                 }
             }
             if constexpr (EDGE) {
@@ -362,17 +350,31 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
             }
         }
         if ((s & (kFlushRows - 1)) == 0) {
+            acc[0] += partk;
+            partk = 0.0f;
 #pragma unroll
-            for (int i = 0; i < kParamSlots; ++i) { acc[i] += part[i]; part[i] = 0.0f; }
+            for (int i = 0; i < 9; ++i) {
+                acc[1 + i] += partw[i].x;
+                acc[10 + i] += partw[i].y;
+                partw[i] = make_float2(0.0f, 0.0f);
+            }
         }
         // shift the windows
-        copy4(ix0, ix1); copy4(iy0, iy1); copy4(ix1, ix2); copy4(iy1, iy2);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) { copy4(gs0[q], gs1[q]); copy4(gs1[q], gsn[q]); }
-        copy6(gx0, gx1); copy6(gy0, gy1); copy6(gx1, gxn); copy6(gy1, gyn);
+        for (int j = 0; j < 4; ++j) {
+            I0[j] = I1[j]; I1[j] = I2[j];
+            gs0[j] = gs1[j]; gs1[j] = gsn[j];
+            gq0[j] = gq1[j]; gq1[j] = gqn[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { gi0[i] = gi1[i]; gi1[i] = gin[i]; }
     }
+    acc[0] += partk;
 #pragma unroll
-    for (int i = 0; i < kParamSlots; ++i) acc[i] += part[i];
+    for (int i = 0; i < 9; ++i) {
+        acc[1 + i] += partw[i].x;
+        acc[10 + i] += partw[i].y;
+    }
     cp_async_wait<0>();
 }
 

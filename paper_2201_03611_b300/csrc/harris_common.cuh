@@ -7,9 +7,13 @@
 //   * each lane owns kCols = 4 adjacent columns; lanes 1..30 produce output, lanes 0 and 31
 //     only provide the 2-column halo each stencil needs (read from neighbours by warp
 //     shuffles, so no shared-memory round trip and no block-wide barrier is needed);
-//   * the lane's 4 input pixels of each row are staged through a per-lane ring of NS rows in
-//     shared memory with cp.async (the toMem(Local) choice), so NS-1 rows are always in
-//     flight while the current one is computed;
+//   * the lane's 4 input pixels of each row are staged through a ring of NS rows in shared
+//     memory with cp.async (the toMem(Local) choice), so NS-1 rows are always in flight while
+//     the current one is computed; a slot holds the 32 lanes' chunks side by side (lane
+//     stride 48 bytes for float32), so the 16-byte shared loads of a quarter-warp hit 8
+//     distinct 16-byte bank groups;
+//   * arithmetic is float32; the x and y halves of the Sobel and adjoint stencils run as
+//     packed float32x2 operations (each half rounds exactly like the scalar operation);
 //   * per-stage clamp padding is applied where it matters: at the image border, the value a
 //     stencil reads beyond the edge is replaced by the edge value of THAT stage (gray, the
 //     vertical product sums, ...), which is exactly pad_clamp before each slide2D.
@@ -92,7 +96,8 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename T, int NS, bool EDGE, bool ALIGNED>
 struct PixelRows {
     static constexpr int kChunk = sizeof(T) == 4 ? 16 : 8;
-    T* ring;         // this lane's NS x 12 elements
+    static constexpr int kSlot = kLanes * 12;  // elements per ring slot (all 32 lanes)
+    T* ring;         // this lane's 12 elements of slot 0; slot s is ring + s * kSlot
     const T* img;
     int64_t pitch;   // elements
     int x;           // first column of the lane
@@ -109,7 +114,7 @@ struct PixelRows {
     __device__ __forceinline__ void fetch(int slot, int yc) const {
         if constexpr (ALIGNED) {
             const char* src = reinterpret_cast<const char*>(img + (int64_t)yc * pitch + (int64_t)x * 3);
-            uint32_t dst = smem_u32(ring + slot * 12);
+            uint32_t dst = smem_u32(ring + slot * kSlot);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 int nb = kChunk;
@@ -129,14 +134,14 @@ struct PixelRows {
     __device__ __forceinline__ void read(int slot, int yc, float v[12]) const {
         if constexpr (ALIGNED) {
             if constexpr (sizeof(T) == 4) {
-                const float4* s = reinterpret_cast<const float4*>(ring + slot * 12);
+                const float4* s = reinterpret_cast<const float4*>(ring + slot * kSlot);
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     float4 q = s[i];
                     v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
                 }
             } else {
-                const uint2* s = reinterpret_cast<const uint2*>(ring + slot * 12);
+                const uint2* s = reinterpret_cast<const uint2*>(ring + slot * kSlot);
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     uint2 q = s[i];
@@ -170,11 +175,19 @@ __device__ __forceinline__ void make_row6(const float c[4], float r6[6]) {
     r6[1] = c[0]; r6[2] = c[1]; r6[3] = c[2]; r6[4] = c[3];
     r6[5] = __shfl_down_sync(kFull, c[0], 1);
 }
+__device__ __forceinline__ void make_row6(const float2 c[4], float2 r6[6]) {
+    r6[0].x = __shfl_up_sync(kFull, c[3].x, 1);
+    r6[0].y = __shfl_up_sync(kFull, c[3].y, 1);
+    r6[1] = c[0]; r6[2] = c[1]; r6[3] = c[2]; r6[4] = c[3];
+    r6[5].x = __shfl_down_sync(kFull, c[0].x, 1);
+    r6[5].y = __shfl_down_sync(kFull, c[0].y, 1);
+}
 
 // pad_clamp at this stage: the value at column -1 becomes the value at column 0 and the
 // value at column W becomes the value at column W-1. Only the stencil reads of in-image
 // columns matter, and those read at most one column beyond the edge.
-__device__ __forceinline__ void clamp_row6(float r6[6], int x, int W) {
+template <typename V>
+__device__ __forceinline__ void clamp_row6(V r6[6], int x, int W) {
     if (x == 0) r6[0] = r6[1];
 #pragma unroll
     for (int p = 1; p < 6; ++p)
@@ -185,59 +198,50 @@ __device__ __forceinline__ float gray_of(float r, float g, float b) {
     return fmaf(kGrayB, b, fmaf(kGrayG, g, kGrayR * r));
 }
 
-// Loop-invariant parameters, read once per warp from device memory.
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// Loop-invariant parameters, read once per warp from device memory: w[k] = (Wx[k], Wy[k]).
 struct Params {
-    float wx[9], wy[9], kappa;
+    float2 w[9];
+    float kappa;
 };
 
 __device__ __forceinline__ void load_params(Params& P, const float* wx, const float* wy, const float* kappa) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) { P.wx[i] = __ldg(wx + i); P.wy[i] = __ldg(wy + i); }
+    for (int i = 0; i < 9; ++i) P.w[i] = make_float2(__ldg(wx + i), __ldg(wy + i));
     P.kappa = __ldg(kappa);
 }
 
 // A2 on one lane: Sobel correlation of three 6-wide gray rows (r0 = row above) at the lane's
-// 4 columns, written with explicit fused multiply-adds so every kernel that calls it gets the
-// same bits.
+// 4 columns; I[j] = (Ix, Iy). Each half is the scalar fused multiply-add chain over the taps
+// in row-major order, so every kernel that calls this gets the same bits.
 __device__ __forceinline__ void sobel(const Params& P, const float r0[6], const float r1[6], const float r2[6],
-                                      float ix[4], float iy[4]) {
+                                      float2 I[4]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float ax = 0.0f, ay = 0.0f;
+        float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            ax = fmaf(P.wx[b], r0[j + b], ax);
-            ay = fmaf(P.wy[b], r0[j + b], ay);
-        }
+        for (int b = 0; b < 3; ++b) acc = __ffma2_rn(P.w[b], dup2(r0[j + b]), acc);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            ax = fmaf(P.wx[3 + b], r1[j + b], ax);
-            ay = fmaf(P.wy[3 + b], r1[j + b], ay);
-        }
+        for (int b = 0; b < 3; ++b) acc = __ffma2_rn(P.w[3 + b], dup2(r1[j + b]), acc);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            ax = fmaf(P.wx[6 + b], r2[j + b], ax);
-            ay = fmaf(P.wy[6 + b], r2[j + b], ay);
-        }
-        ix[j] = ax;
-        iy[j] = ay;
+        for (int b = 0; b < 3; ++b) acc = __ffma2_rn(P.w[6 + b], dup2(r2[j + b]), acc);
+        I[j] = acc;
     }
 }
 
-// A3 + vertical half of A4: the three product sums over Sobel rows a (above), m, b (below),
-// each already clamped by the caller: v = a*a' + b*b' + m*m' per plane.
-__device__ __forceinline__ void vertical_products(const float ax[4], const float ay[4], const float mx[4],
-                                                  const float my[4], const float bx[4], const float by[4],
-                                                  float v[3][4]) {
+// A3 + vertical half of A4: the product sums over Sobel rows a (above), m, b (below), each
+// already clamped by the caller. v2 = (xx, yy) sums, vxy = xy sums.
+__device__ __forceinline__ void vertical_products(const float2 a[4], const float2 m[4], const float2 b[4],
+                                                  float2 v2[4], float vxy[4]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v[0][j] = fmaf(ax[j], ax[j], fmaf(bx[j], bx[j], __fmul_rn(mx[j], mx[j])));
-        v[1][j] = fmaf(ax[j], ay[j], fmaf(bx[j], by[j], __fmul_rn(mx[j], my[j])));
-        v[2][j] = fmaf(ay[j], ay[j], fmaf(by[j], by[j], __fmul_rn(my[j], my[j])));
+        v2[j] = __ffma2_rn(a[j], a[j], __ffma2_rn(b[j], b[j], __fmul2_rn(m[j], m[j])));
+        vxy[j] = fmaf(a[j].x, a[j].y, fmaf(b[j].x, b[j].y, __fmul_rn(m[j].x, m[j].y)));
     }
 }
 
-// Horizontal half of A4 on one plane (with the per-stage clamp on EDGE warps).
+// Horizontal half of a 3x3 box sum (with the per-stage clamp on EDGE warps).
 template <bool EDGE>
 __device__ __forceinline__ void horizontal_box(const float v[4], float s[4], int x, int W) {
     float r6[6];
@@ -245,6 +249,14 @@ __device__ __forceinline__ void horizontal_box(const float v[4], float s[4], int
     if constexpr (EDGE) clamp_row6(r6, x, W);
 #pragma unroll
     for (int j = 0; j < 4; ++j) s[j] = __fadd_rn(__fadd_rn(r6[j], r6[j + 1]), r6[j + 2]);
+}
+template <bool EDGE>
+__device__ __forceinline__ void horizontal_box(const float2 v[4], float2 s[4], int x, int W) {
+    float2 r6[6];
+    make_row6(v, r6);
+    if constexpr (EDGE) clamp_row6(r6, x, W);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = __fadd2_rn(__fadd2_rn(r6[j], r6[j + 1]), r6[j + 2]);
 }
 
 // A5 in float32 (det - kappa * trace^2 cancels, so it is never done in a narrower type).

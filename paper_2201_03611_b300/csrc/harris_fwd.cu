@@ -11,19 +11,19 @@ namespace shine {
 namespace {
 
 template <typename TI, typename TO, int NS, bool ALIGNED>
-__global__ void __launch_bounds__(kFwdThreads) harris_fwd_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_kernel(FwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kFwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
-    TI* ring = reinterpret_cast<TI*>(smem_raw) + (warp * 32 + lane) * NS * 12;
+    TI* ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
     Params P;
     load_params(P, a.wx, a.wy, a.kappa);
     // This warp's equal share of the (segment, row) units, walked segment by segment.
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    balanced_slice(rows * a.nseg, a.nwarps, gw, lo, hi);
+    warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
     while (lo < hi) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
@@ -55,6 +55,8 @@ cudaError_t launch_fwd_t(FwdArgs a, cudaStream_t s) {
     auto kern = a.aligned ? harris_fwd_kernel<TI, TO, NS, true> : harris_fwd_kernel<TI, TO, NS, false>;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     if (units <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int64_t t = resident_warps(kern, kFwdThreads, smem);
     t = std::min<int64_t>(t, std::max<int64_t>(1, units / kFwdMinRows));
     a.nwarps = (int)t;

@@ -1,9 +1,9 @@
 // Forward strip: one warp computes R over one (column segment, row band) of one image.
 //
-// Per output row y it stages one new image row, makes its gray row, the Sobel/product row
-// y+1, adds the three product rows around y (the slide2D+reduce of A4 done vertically in
-// registers first, then horizontally with two shuffles per plane), and stores R[y]. HBM
-// traffic is the image once and R once; nothing else leaves the registers.
+// Rows are processed RB at a time: one wait for RB staged image rows, their gray rows and
+// Sobel rows, then the RB product/box/response rows. The RB rows' work is independent
+// (instruction-level parallelism for a warp that otherwise waits on shuffle and shared-memory
+// latency). HBM traffic is the image once and R once; nothing else leaves the registers.
 #pragma once
 
 #include "harris_common.cuh"
@@ -11,78 +11,89 @@
 
 namespace shine {
 
-template <typename TI, typename TO, int NS, bool EDGE, bool ALIGNED>
+template <typename TI, typename TO, int NS, bool EDGE, bool ALIGNED, int RB = kFwdRowsPerBlock>
 __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0,
                                           int y1, TI* ring) {
+    // Staging: kFirst rows are put in flight up front; every block then reads RB rows and stages
+    // RB more. Before block b, rows up to 3 + RB (b + 1) + (kFirst - 4) have been issued while
+    // rows up to 3 + RB (b + 1) are needed, so waiting until at most kFirst - 4 groups are
+    // pending leaves that many rows in flight. Rows staged after a block's reads go to slots of
+    // rows consumed in earlier blocks (kFirst + 2 RB - 4 <= NS).
+    constexpr int kFirst = (NS + 4 - 2 * RB) < NS ? (NS + 4 - 2 * RB) : NS;
+    static_assert(kFirst - 4 >= RB, "the ring must hold at least one block in flight");
     const int H = a.H, W = a.W;
     PixelRows<TI, NS, EDGE, ALIGNED> rows(ring, static_cast<const TI*>(a.img), a.img_pitch, x, W);
-    const int nrows = y1 - y0 + 4;  // gray rows y0-2 .. y1+1 (clamped)
+    const int nblocks = (y1 - y0 + RB - 1) / RB;
+    const int nrows = 4 + RB * nblocks;  // gray rows y0-2 .. y0+1+RB*nblocks (clamped)
     const int r_first = y0 - 2;
 
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) {
-        if (s < nrows) rows.fetch(s, clampi(r_first + s, H));
+    for (int q = 0; q < kFirst; ++q) {
+        if (q < nrows) rows.fetch(q % NS, clampi(r_first + q, H));
         cp_async_commit();
     }
+    int next = kFirst;  // next sequence row to stage
 
-    // Gray row number s of the sequence, 6 columns wide, clamped at the image border.
-    auto gray_row = [&](int s, float g6[6]) {
-        cp_async_wait<NS - 2>();
+    auto gray6 = [&](int q, float g6[6]) {
         float v[12];
-        rows.read(s % NS, clampi(r_first + s, H), v);
+        rows.read(q % NS, clampi(r_first + q, H), v);
         float c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = gray_of(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
-        int sn = s + NS - 1;
-        if (sn < nrows) rows.fetch(sn % NS, clampi(r_first + sn, H));
-        cp_async_commit();
         make_row6(c, g6);
         if constexpr (EDGE) clamp_row6(g6, x, W);
     };
-
-    float g0[6], g1[6], g2[6];
-    float ixa[4], iya[4], ixb[4], iyb[4], ixc[4], iyc[4];  // Sobel rows y-1, y, y+1
-    gray_row(0, g0);
-    gray_row(1, g1);
-    gray_row(2, g2);
-    sobel(P, g0, g1, g2, ixa, iya);  // row y0-1 (replaced by row y0 at the top border)
+    auto stage_more = [&]() {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
-    gray_row(3, g2);
-    sobel(P, g0, g1, g2, ixb, iyb);  // row y0
+        for (int i = 0; i < RB; ++i) {
+            if (next < nrows) rows.fetch(next % NS, clampi(r_first + next, H));
+            cp_async_commit();
+            ++next;
+        }
+    };
+
+    // g[0], g[1]: gray rows y, y+1 of the coming block; I[0], I[1]: Sobel rows y-1, y.
+    float g[RB + 2][6];
+    float2 I[RB + 2][4];
+    {
+        cp_async_wait<kFirst - 4>();  // sequence rows 0..3 landed
+        float g0[6], g1[6];
+        gray6(0, g0);
+        gray6(1, g1);
+        gray6(2, g[0]);
+        gray6(3, g[1]);
+        stage_more();
+        sobel(P, g0, g1, g[0], I[0]);  // row y0-1 (replaced by row y0 at the top border)
+        sobel(P, g1, g[0], g[1], I[1]);  // row y0
+    }
 
     TO* out = static_cast<TO*>(a.out);
     const bool producer = lane >= 1 && lane <= 30;
 
-#pragma unroll 2
-    for (int y = y0; y < y1; ++y) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
-        gray_row(y - y0 + 4, g2);
-        sobel(P, g0, g1, g2, ixc, iyc);  // row y+1 (replaced by row y at the bottom border)
-
+    auto emit = [&](int y, const float2 Iu[4], const float2 Im[4], const float2 Id[4]) {
+        if (y >= y1) return;
         // A3 + A4: products summed over rows y-1, y, y+1, clamped at their own stage.
-        float v[3][4];
+        float2 v2[4];
+        float vxy[4];
         if (y == 0 || y == H - 1) {
-            float ax[4], ay[4], bx[4], by[4];
+            float2 A[4], B[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                ax[j] = (y == 0) ? ixb[j] : ixa[j];
-                ay[j] = (y == 0) ? iyb[j] : iya[j];
-                bx[j] = (y == H - 1) ? ixb[j] : ixc[j];
-                by[j] = (y == H - 1) ? iyb[j] : iyc[j];
+                A[j] = (y == 0) ? Im[j] : Iu[j];
+                B[j] = (y == H - 1) ? Im[j] : Id[j];
             }
-            vertical_products(ax, ay, ixb, iyb, bx, by, v);
+            vertical_products(A, Im, B, v2, vxy);
         } else {
-            vertical_products(ixa, iya, ixb, iyb, ixc, iyc, v);
+            vertical_products(Iu, Im, Id, v2, vxy);
         }
-        float s3[3][4];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) horizontal_box<EDGE>(v[q], s3[q], x, W);
+        float2 s2[4];
+        float sxy[4];
+        horizontal_box<EDGE>(v2, s2, x, W);
+        horizontal_box<EDGE>(vxy, sxy, x, W);
         // A5
         float R[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) R[j] = response(s3[0][j], s3[1][j], s3[2][j], P.kappa);
+        for (int j = 0; j < 4; ++j) R[j] = response(s2[j].x, sxy[j], s2[j].y, P.kappa);
         if (producer) {
             const int yo = y - a.oy;
             TO* orow = out + (int64_t)yo * a.out_pitch;
@@ -103,10 +114,26 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
                 }
             }
         }
+    };
+
+#pragma unroll 1
+    for (int b = 0; b < nblocks; ++b) {
+        const int q = 4 + RB * b;  // first sequence row of this block (gray row y+2)
+        const int y = y0 + RB * b;
+        cp_async_wait<kFirst - 4>();  // sequence rows q .. q+RB-1 landed
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            ixa[j] = ixb[j]; iya[j] = iyb[j];
-            ixb[j] = ixc[j]; iyb[j] = iyc[j];
+        for (int i = 0; i < RB; ++i) gray6(q + i, g[2 + i]);
+        stage_more();
+#pragma unroll
+        for (int i = 0; i < RB; ++i) sobel(P, g[i], g[i + 1], g[i + 2], I[2 + i]);  // rows y+1 ..
+#pragma unroll
+        for (int i = 0; i < RB; ++i) emit(y + i, I[i], I[i + 1], I[i + 2]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) g[i][c] = g[RB + i][c];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) I[i][j] = I[RB + i][j];
         }
     }
     cp_async_wait<0>();

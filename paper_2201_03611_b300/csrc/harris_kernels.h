@@ -10,10 +10,34 @@ constexpr int kCols = 4;                       // pixels per lane
 constexpr int kLanes = 32;
 constexpr int kSegLoad = kLanes * kCols;       // 128 staged columns per warp segment
 constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp segment
+// Compile-time tuning of the kernels (each has a default; the values are chosen by measurement).
+#ifndef SHINE_FWD_STAGES
+#define SHINE_FWD_STAGES 8        // staged image rows of the forward ring
+#endif
+#ifndef SHINE_FWD_ROWS
+#define SHINE_FWD_ROWS 2          // rows per forward block
+#endif
+#ifndef SHINE_FWD_MIN_BLOCKS
+#define SHINE_FWD_MIN_BLOCKS 1    // resident CTAs per SM the forward register budget must allow
+#endif
+#ifndef SHINE_BWD_STAGES
+#define SHINE_BWD_STAGES 4        // staged rows of the backward ring
+#endif
+#ifndef SHINE_BWD_UNROLL
+#define SHINE_BWD_UNROLL 1        // unrolling of the backward row loop
+#endif
+#ifndef SHINE_FWD_BAND_MAJOR
+#define SHINE_FWD_BAND_MAJOR 1    // forward: equal row bands across all segments
+#endif
+#ifndef SHINE_BWD_BAND_MAJOR
+#define SHINE_BWD_BAND_MAJOR 0    // backward: even segment-major slices
+#endif
 constexpr int kFwdThreads = 128;  // 4 warps per CTA
-constexpr int kFwdStages = 4;     // staged image rows per lane (cp.async ring)
+constexpr int kFwdStages = SHINE_FWD_STAGES;
+constexpr int kFwdRowsPerBlock = SHINE_FWD_ROWS;
 constexpr int kBwdThreads = 128;
-constexpr int kBwdStages = 4;
+constexpr int kBwdStages = SHINE_BWD_STAGES;
+constexpr int kBwdUnroll = SHINE_BWD_UNROLL;
 constexpr int kParamSlots = 19;   // d kappa, d Wx[9], d Wy[9]
 
 // Geometry shared by all kernels: which output region of the image a launch covers and how
@@ -35,6 +59,27 @@ __host__ __device__ inline void balanced_slice(int64_t n, int64_t t, int64_t w, 
     const int64_t q = n / t, rem = n % t;
     lo = q * w + (w < rem ? w : rem);
     hi = lo + q + (w < rem ? 1 : 0);
+}
+
+// Work of warp w among t warps over nseg segments x rows rows, as (segment, row) units in
+// segment-major order: [lo, hi). Band-major: when t >= nseg, warp w takes segment w % nseg and
+// the (w / nseg)-th of t / nseg equal row bands, so the warps of one band walk the same rows
+// at the same time (whole image rows, good DRAM page locality) and every warp has the same
+// work; surplus warps (w >= nseg * (t / nseg)) get nothing. Otherwise the units are split
+// evenly in segment-major order.
+__host__ __device__ inline void warp_work(bool band_major, int64_t nseg, int64_t rows, int64_t t, int64_t w,
+                                          int64_t& lo, int64_t& hi) {
+    if (band_major && t >= nseg) {
+        const int64_t nb = t / nseg;
+        if (w >= nb * nseg) { lo = hi = 0; return; }
+        const int64_t seg = w % nseg, band = w / nseg;
+        int64_t r0, r1;
+        balanced_slice(rows, nb, band, r0, r1);
+        lo = seg * rows + r0;
+        hi = seg * rows + r1;
+        return;
+    }
+    balanced_slice(nseg * rows, t, w, lo, hi);
 }
 
 struct FwdArgs : Geometry {
