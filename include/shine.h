@@ -204,6 +204,13 @@ SHINE_API const char* shine_status_string(shine_status s);
 /* The cudaError_t (as int) of the last SHINE_ERR_CUDA returned on this host thread. */
 SHINE_API int shine_last_cuda_error(void);
 
+/*
+ * Whether the last backward pass run on this workspace gave up waiting for its staged rows
+ * (*failed = 1; its results are then not valid) -- every wait in the kernels is bounded, so a
+ * fault of the copy engine surfaces here instead of as a hang. Synchronises with the device.
+ */
+SHINE_API shine_status shine_workspace_status(const void* workspace, int* failed);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         "shine_status_string": (ctypes.c_char_p, [f]),
         "shine_tune_key": (ctypes.c_int, [ctypes.c_char_p, sz]),
         "shine_last_cuda_error": (ctypes.c_int, []),
+        "shine_workspace_status": (st, [p, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)

@@ -60,12 +60,16 @@ void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_imag
 Geometry fwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
     fill_geometry(g, H, W, border, false, (int)H);
+    g.x0 = kBwdSegmentOrigin;
+    g.nseg = (g.xhi - g.x0 + kSegOut - 1) / kSegOut;
     return g;
 }
 
 Geometry bwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
     fill_geometry(g, H, W, border, true, (int)H);
+    g.x0 = kBwdSegmentOrigin;
+    g.nseg = (g.xhi - g.x0 + kSegOut - 1) / kSegOut;
     return g;
 }
 
@@ -95,6 +99,15 @@ const char* shine_status_string(shine_status s) {
 }
 
 int shine_last_cuda_error(void) { return g_last_cuda_error; }
+
+shine_status shine_workspace_status(const void* workspace, int* failed) {
+    if (!workspace || !failed) return SHINE_ERR_INVALID_ARG;
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpy(&v, workspace, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    *failed = v != 0;
+    return SHINE_OK;
+}
 
 shine_status shine_output_shape(int64_t H, int64_t W, shine_border border, int64_t* H_out, int64_t* W_out) {
     if (!H_out || !W_out) return SHINE_ERR_INVALID_ARG;
@@ -127,6 +140,8 @@ shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t i
     const size_t chunk = si == 4 ? 16 : 8;
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.out_vec = border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
+    a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
+    a.err = nullptr;
     return cuda_status(launch_harris_fwd(a, dt, out_dt, static_cast<cudaStream_t>(stream)));
 }
 
@@ -135,7 +150,7 @@ shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border bor
     shine_status st = check_shape(H, W, border);
     if (st != SHINE_OK) return st;
     Geometry g = bwd_geometry(H, W, border);
-    *bytes = (size_t)kParamSlots * (size_t)bwd_max_warps(g) * sizeof(double);
+    *bytes = kWorkspaceHeader + (size_t)kParamSlots * (size_t)bwd_max_warps(g) * sizeof(double);
     return SHINE_OK;
 }
 
@@ -165,7 +180,7 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     BwdArgs a;
     static_cast<Geometry&>(a) = bwd_geometry(H, W, border);
     const int64_t max_warps = bwd_max_warps(a);
-    const size_t need = (size_t)kParamSlots * (size_t)max_warps * sizeof(double);
+    const size_t need = kWorkspaceHeader + (size_t)kParamSlots * (size_t)max_warps * sizeof(double);
     if (!workspace || ws_bytes < need) return SHINE_ERR_WORKSPACE;
     if (!aligned_to(workspace, 16)) return SHINE_ERR_ALIGNMENT;
     if (!out && !grad_img && !grad_kappa && !grad_wx && !grad_wy) return SHINE_OK;
@@ -173,14 +188,19 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     a.gout = grad_out; a.gout_pitch = gout_pitch; a.gho = (int)Ho; a.gwo = (int)Wo;
     a.gimg = grad_img; a.gimg_pitch = gimg_pitch;
     a.kappa = kappa; a.wx = wx; a.wy = wy;
-    a.partials = static_cast<double*>(workspace);
+    a.err = static_cast<unsigned int*>(workspace);
+    a.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + kWorkspaceHeader);
     const size_t chunk = si == 4 ? 16 : 8;
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.g_aligned = border == SHINE_CLAMP && aligned_to(grad_out, 4 * sg) && ((size_t)gout_pitch * sg) % (4 * sg) == 0;
     a.gimg_vec = grad_img && aligned_to(grad_img, chunk) && ((size_t)gimg_pitch * si) % chunk == 0;
+    a.tma = SHINE_BWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0 &&
+            aligned_to(grad_out, 16) && ((size_t)gout_pitch * sg) % 16 == 0 && border == SHINE_CLAMP;
     a.rout = out; a.rout_pitch = out_pitch;
     a.rout_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * si) && ((size_t)out_pitch * si) % (4 * si) == 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = cuda_status(cudaMemsetAsync(a.err, 0, sizeof(unsigned int), s));
+    if (st != SHINE_OK) return st;
     int used = 0;
     st = cuda_status(launch_harris_bwd(a, dt, gout_dt, (int)max_warps, s, &used));
     if (st != SHINE_OK) return st;

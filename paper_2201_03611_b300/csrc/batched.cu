@@ -44,7 +44,7 @@ namespace shine {
 namespace {
 
 constexpr int kBatchThreads = 128;
-template <bool FWD_BWD> constexpr int batch_stages() { return FWD_BWD ? kBwdStages : kFwdStages; }
+template <bool FWD_BWD> constexpr int batch_stages() { return FWD_BWD ? kBwdStages : 0; }
 
 struct BatchArgs {
     const shine_image_desc* descs;
@@ -108,14 +108,16 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
             a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
             a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);
             a.out_vec = !b.valid && dev_aligned(d.out, d.out_pitch, sizeof(T), 4 * sizeof(T));
+            a.tma = 0;
+            a.err = nullptr;
             const int xb = seg * kSegOut, x = xb - 4 + 4 * lane;
             const int y0 = a.ylo + band * a.band_rows, y1 = min(y0 + a.band_rows, a.yhi);
             const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > W) || a.valid;
             if (a.aligned) {
-                if (edge) fwd_strip<T, T, NS, true, true>(a, P, lane, x, y0, y1, ring);
-                else fwd_strip<T, T, NS, false, true>(a, P, lane, x, y0, y1, ring);
+                if (edge) fwd_strip<T, T, kFwdStages, true, true>(a, P, lane, x, y0, y1);
+                else fwd_strip<T, T, kFwdStages, false, true>(a, P, lane, x, y0, y1);
             } else {
-                fwd_strip<T, T, NS, true, false>(a, P, lane, x, y0, y1, ring);
+                fwd_strip<T, T, kFwdStages, true, false>(a, P, lane, x, y0, y1);
             }
         } else {
             BwdArgs a;
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
             a.gimg = d.grad_img; a.gimg_pitch = d.gimg_pitch;
             a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
             a.partials = nullptr;
+            a.err = nullptr;
+            a.tma = 0;
             a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);
             a.g_aligned = !b.valid && dev_aligned(d.grad_out, d.gout_pitch, sizeof(T), 4 * sizeof(T));
             a.gimg_vec = d.grad_img != nullptr && dev_aligned(d.grad_img, d.gimg_pitch, sizeof(T), chunk);

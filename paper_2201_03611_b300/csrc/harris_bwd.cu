@@ -30,27 +30,38 @@ namespace shine {
 
 namespace {
 
-template <typename TI, typename TG, int NS, bool ALIGNED, bool GALIGNED, bool WITH_R>
+template <typename TI, typename TG, int NS, bool ALIGNED, bool GALIGNED, bool WITH_R, bool TMA>
 __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kBwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
     TI* ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
-    TG* gring = reinterpret_cast<TG*>(smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI)) +
-                warp * NS * kLanes * 4 + lane * 4;
+    unsigned char* gbase = smem_raw + (size_t)kBwdThreads * NS * 12 * sizeof(TI);
+    TG* gring = reinterpret_cast<TG*>(gbase) + warp * NS * kLanes * 4 + lane * 4;
+    BulkState bulk;
+    bulk.seq = 0;
+    bulk.failed = false;
+    if constexpr (TMA) {
+        uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (size_t)kBwdThreads * NS * 4 * sizeof(TG)) + warp * NS;
+        bulk.bars = smem_u32(bars);
+        if (lane == 0)
+            for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+        mbar_init_fence();
+        __syncwarp();
+    }
     Params P;
     load_params(P, a.wx, a.wy, a.kappa);
     float acc[kParamSlots];
 #pragma unroll
     for (int i = 0; i < kParamSlots; ++i) acc[i] = 0.0f;
     TI* rout = static_cast<TI*>(a.rout);
-    // This warp's equal share of the (segment, row) units, walked segment by segment.
+    // This warp's share of the (segment, row) units, walked segment by segment.
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
     warp_work(SHINE_BWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
-    while (lo < hi) {
+    while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
         const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
@@ -58,13 +69,15 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
         const int x = xb - 4 + 4 * lane;
         const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W);
         if (edge)
-            bwd_strip<TI, TG, NS, true, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
-                                                                   gring, acc, rout, a.rout_pitch, a.rout_vec);
+            bwd_strip<TI, TG, NS, true, ALIGNED, GALIGNED, WITH_R, false>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
+                                                                          gring, acc, rout, a.rout_pitch, a.rout_vec);
         else
-            bwd_strip<TI, TG, NS, false, ALIGNED, GALIGNED, WITH_R>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
-                                                                    gring, acc, rout, a.rout_pitch, a.rout_vec);
+            bwd_strip<TI, TG, NS, false, ALIGNED, GALIGNED, WITH_R, TMA>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring,
+                                                                         gring, acc, rout, a.rout_pitch, a.rout_vec,
+                                                                         &bulk);
         lo += r1 - r0;
     }
+    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
     // Warp partials in float64, lanes 0 and 31 excluded by selection (their values may be
     // unrelated to this warp's pixels).
     const bool producer = lane >= 1 && lane <= 30;
@@ -91,16 +104,16 @@ int resident_warps(K kernel, int threads, size_t smem) {
 template <typename TI, typename TG>
 cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
     constexpr int NS = kBwdStages;
-    const size_t smem = (size_t)kBwdThreads * NS * (12 * sizeof(TI) + 4 * sizeof(TG));
+    const size_t smem = (size_t)kBwdThreads * NS * (12 * sizeof(TI) + 4 * sizeof(TG)) + (kBwdThreads / 32) * NS * 8;
     const bool wr = a.rout != nullptr;
     void (*kern)(BwdArgs);
-    if (a.aligned && a.g_aligned)
-        kern = wr ? harris_bwd_kernel<TI, TG, NS, true, true, true> : harris_bwd_kernel<TI, TG, NS, true, true, false>;
-    else if (a.aligned)
-        kern = wr ? harris_bwd_kernel<TI, TG, NS, true, false, true> : harris_bwd_kernel<TI, TG, NS, true, false, false>;
-    else
-        kern = wr ? harris_bwd_kernel<TI, TG, NS, false, false, true>
-                  : harris_bwd_kernel<TI, TG, NS, false, false, false>;
+#define SHINE_BWD_PICK(AL, GA, TMA_)                                                            \
+    kern = wr ? harris_bwd_kernel<TI, TG, NS, AL, GA, true, TMA_> : harris_bwd_kernel<TI, TG, NS, AL, GA, false, TMA_>
+    if (a.aligned && a.g_aligned && a.tma) SHINE_BWD_PICK(true, true, true);
+    else if (a.aligned && a.g_aligned) SHINE_BWD_PICK(true, true, false);
+    else if (a.aligned) SHINE_BWD_PICK(true, false, false);
+    else SHINE_BWD_PICK(false, false, false);
+#undef SHINE_BWD_PICK
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

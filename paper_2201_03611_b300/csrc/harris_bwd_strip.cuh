@@ -2,6 +2,8 @@
 // row band) of one image; see harris_bwd.cu for the adjoint chain B1-B6.
 #pragma once
 
+#include <type_traits>
+
 #include "harris_common.cuh"
 #include "harris_kernels.h"
 
@@ -71,10 +73,23 @@ struct CotRows {
 //
 // acc receives this strip's parameter cotangents: acc[0] = d kappa, acc[1 + t] = d Wx[t],
 // acc[10 + t] = d Wy[t] (t = 3a + b), for the rows [y0, y1) and producer columns it owns.
-template <typename TI, typename TG, int NS, bool EDGE, bool ALIGNED, bool GALIGNED, bool WITH_R = false>
+// Staging of the strip's rows. TMA: lane 0 moves each row's whole image segment and cotangent
+// segment with two bulk copies completing on the slot's mbarrier (interior segments with
+// 16-byte aligned rows); otherwise every lane stages its own chunks with cp.async. Both fill the
+// same slot layout (lane stride 12 image / 4 cotangent elements). Bulk staging keeps the copy
+// engine streaming at the full HBM rate with few warps; the per-lane path tops out lower.
+struct BulkState {
+    uint32_t bars;     // shared address of this warp's NS barriers
+    uint32_t seq;      // rows staged by this warp so far (slot = seq % NS, phase = seq / NS)
+    bool failed;       // a bounded wait gave up
+};
+
+template <typename TI, typename TG, int NS, bool EDGE, bool ALIGNED, bool GALIGNED, bool WITH_R = false,
+          bool TMA = false>
 __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int lane, int x, int y0,
                                           int y1, TI* ring, TG* gring, float acc[kParamSlots],
-                                          TI* rout = nullptr, int64_t rpitch = 0, bool rvec = false) {
+                                          TI* rout = nullptr, int64_t rpitch = 0, bool rvec = false,
+                                          BulkState* bulk = nullptr) {
     const int H = a.H, W = a.W;
     const bool producer = lane >= 1 && lane <= 30;
     PixelRows<TI, NS, EDGE, ALIGNED> rows(ring, static_cast<const TI*>(a.img), a.img_pitch, x, W);
@@ -82,38 +97,88 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                                           a.oy, a.gho, a.gwo);
     const int r_first = y0 - 4;
     const int nrows = y1 - y0 + 8;  // image rows y0-4 .. y1+3, cotangent rows y0-6 .. y1+1
+    const uint32_t seq0 = TMA ? bulk->seq : 0u;
 
     // Column validity of the lane's 4 columns (only EDGE warps can have invalid ones).
     bool cin[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) cin[j] = !EDGE || (x + j >= 0 && x + j < W);
 
-#pragma unroll
-    for (int s = 0; s < NS - 1; ++s) {
-        if (s < nrows) {
-            rows.fetch(s, clampi(r_first + s, H));
-            grows.fetch(s, r_first + s - 2);
+    // Bulk staging: the warp's segment starts 4 columns left of the lane-1 column.
+    const int xs = x - 4 * lane;
+    constexpr uint32_t kImgBytes = kSegLoad * 3 * sizeof(TI), kCotBytes = kSegLoad * sizeof(TG);
+    int last_issued = -1, last_done = -1;  // bulk staging: rows issued / waited for successfully
+    auto bulk_fetch = [&](int s) {
+        if constexpr (TMA) {
+            if (s < nrows) last_issued = s;
+            if (lane == 0 && s < nrows) {
+                const uint32_t q = seq0 + s, slot = q % NS, bar = bulk->bars + 8 * slot;
+                const int r = r_first + s, gy = r - 2;
+                const bool g_in = gy >= 0 && gy < a.gho;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, kImgBytes + (g_in ? kCotBytes : 0));
+                const TI* src = static_cast<const TI*>(a.img) + (int64_t)clampi(r, H) * a.img_pitch + (int64_t)xs * 3;
+                bulk_copy_g2s(smem_u32(ring - lane * 12 + slot * PixelRows<TI, NS, EDGE, ALIGNED>::kSlot), src,
+                              kImgBytes, bar);
+                if (g_in) {
+                    const TG* gs = static_cast<const TG*>(a.gout) + (int64_t)gy * a.gout_pitch + xs;
+                    bulk_copy_g2s(smem_u32(gring - lane * 4 + slot * CotRows<TG, NS, EDGE, GALIGNED>::kSlot), gs,
+                                  kCotBytes, bar);
+                }
+            }
         }
-        cp_async_commit();
+    };
+
+    if constexpr (TMA) {
+#pragma unroll
+        for (int s = 0; s < NS - 1; ++s) bulk_fetch(s);
+    } else {
+#pragma unroll
+        for (int s = 0; s < NS - 1; ++s) {
+            if (s < nrows) {
+                rows.fetch(s, clampi(r_first + s, H));
+                grows.fetch(s, r_first + s - 2);
+            }
+            cp_async_commit();
+        }
     }
 
     // Step s: gray row (6 wide, clamped) of image row r_first + s, and its cotangent row
     // (row - 2), staged NS - 1 steps ahead.
     auto stage_in = [&](int s, float g6[6], float gv[4]) {
-        cp_async_wait<NS - 2>();
         const int r = r_first + s;
         float v[12];
-        rows.read(s % NS, clampi(r, H), v);
-        grows.read(s % NS, r - 2, gv);
+        if constexpr (TMA) {
+            const uint32_t q = seq0 + s, slot = q % NS;
+            const bool ok = __all_sync(kFull, mbar_wait(bulk->bars + 8 * slot, (q / NS) & 1u));
+            if (ok) last_done = s;
+            else bulk->failed = true;
+            rows.read(slot, clampi(r, H), v);
+            const int gy = r - 2;
+            if (gy >= 0 && gy < a.gho) {
+                grows.read(slot, r - 2, gv);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) gv[j] = 0.0f;
+            }
+            __syncwarp();  // every lane has read the slot that the next copy overwrites
+            if (ok) bulk_fetch(s + NS - 1);
+        } else {
+            cp_async_wait<NS - 2>();
+            rows.read(s % NS, clampi(r, H), v);
+            grows.read(s % NS, r - 2, gv);
+        }
         float c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = gray_of(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
-        const int sn = s + NS - 1;
-        if (sn < nrows) {
-            rows.fetch(sn % NS, clampi(r_first + sn, H));
-            grows.fetch(sn % NS, r_first + sn - 2);
+        if constexpr (!TMA) {
+            const int sn = s + NS - 1;
+            if (sn < nrows) {
+                rows.fetch(sn % NS, clampi(r_first + sn, H));
+                grows.fetch(sn % NS, r_first + sn - 2);
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
         make_row6(c, g6);
         if constexpr (EDGE) clamp_row6(g6, x, W);
     };
@@ -150,8 +215,12 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 #pragma unroll
     for (int i = 0; i < 9; ++i) partw[i] = make_float2(0.0f, 0.0f);
 
-#pragma unroll kBwdUnroll
-    for (int s = 2; s < nrows; ++s) {
+    // One step: stage image row r = r_first + s and cotangent row r-2, then B1..B6 for the rows
+    // whose inputs are complete. FAST steps are those whose rows are all interior to the image
+    // and to this strip (no clamp, fold or ownership test is needed); they run back to back in
+    // threes, so the 3-row windows rotate by renaming instead of register moves.
+    auto step = [&](auto fast_tag, int s) {
+        constexpr bool FAST = decltype(fast_tag)::value;
         const int r = r_first + s;
         // shift the gray window down one row and stage row r into G4
 #pragma unroll
@@ -166,7 +235,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         const int sr = r - 2;
         float2 v2[4];
         float vxy[4];
-        if (sr == 0 || sr == H - 1) {
+        if (!FAST && (sr == 0 || sr == H - 1)) {
             float2 A[4], B[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -181,11 +250,11 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         float Sxy[4];
         horizontal_box<EDGE>(v2, S2, x, W);
         horizontal_box<EDGE>(vxy, Sxy, x, W);
-        const bool own_row = sr >= y0 && sr < y1;
+        const bool own_row = FAST || (sr >= y0 && sr < y1);
         if constexpr (WITH_R) {
             // R at row sr (A5), for rows this warp owns inside the forward output region
             const int rlo = a.valid ? 2 : 0, rhi = a.valid ? H - 2 : H;
-            if (rout != nullptr && own_row && producer && sr >= rlo && sr < rhi) {
+            if (rout != nullptr && own_row && producer && (FAST || (sr >= rlo && sr < rhi))) {
                 float R[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) R[j] = response(S2[j].x, Sxy[j], S2[j].y, P.kappa);
@@ -230,7 +299,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         {
             float2 vg2[4];
             float vgq[4];
-            if (k == 0 || k == H - 1) {
+            if (!FAST && (k == 0 || k == H - 1)) {
                 const bool top = k == 0, bot = k == H - 1;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -249,7 +318,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         }
         // B4: gI at row k (zero outside the image: the padded domain of B5).
         float2 gI[4];
-        if (k >= 0 && k < H) {
+        if (FAST || (k >= 0 && k < H)) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float2 i0 = I0[j];
@@ -264,7 +333,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         // B5 (weights): (d Wx[a][b], d Wy[a][b]) += gI(k, c) * G(clamp(k + a - 1), clamp(c + b - 1))
         // for the rows this warp owns (gI is zero outside the image; lanes 0 and 31 are dropped
         // when the warp reduces). Gray rows k-1, k, k+1 are G0, G1, G2.
-        if (k >= y0 && k < y1) {
+        if (FAST || (k >= y0 && k < y1)) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
 #pragma unroll
@@ -281,7 +350,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         // B5 (image) + B6 at row u = r-4: transposed stencil over gI rows u-1 (gi0), u (gi1),
         // u+1 (gin), with the vertical clamp folds, then the horizontal folds, then store.
         const int u = r - 4;
-        if (u >= y0 && gimg != nullptr) {
+        if ((FAST || u >= y0) && gimg != nullptr) {
             float gg[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -295,7 +364,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 }
                 gg[j] = t.x + t.y;
             }
-            if (u == 0 || u == H - 1) {
+            if (!FAST && (u == 0 || u == H - 1)) {
                 // padded row -1 (weights row 0) and row H (weights row 2) fold onto row u
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -349,16 +418,6 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 }
             }
         }
-        if ((s & (kFlushRows - 1)) == 0) {
-            acc[0] += partk;
-            partk = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                acc[1 + i] += partw[i].x;
-                acc[10 + i] += partw[i].y;
-                partw[i] = make_float2(0.0f, 0.0f);
-            }
-        }
         // shift the windows
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -368,6 +427,43 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i) { gi0[i] = gi1[i]; gi1[i] = gin[i]; }
+    };
+    auto flush = [&]() {
+        acc[0] += partk;
+        partk = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            acc[1 + i] += partw[i].x;
+            acc[10 + i] += partw[i].y;
+            partw[i] = make_float2(0.0f, 0.0f);
+        }
+    };
+    const std::integral_constant<bool, false> general{};
+    const std::integral_constant<bool, true> fast{};
+    // Fast steps: u = r - 4 >= max(y0, 2) and S row r - 2 <= min(y1 - 1, H - 3).
+    const int s_a = 8 + (y0 < 2 ? 2 - y0 : 0);
+    const int s_b = (y1 - 3 < H - 5 ? y1 - 3 : H - 5) - y0 + 9;  // exclusive
+    int s = 2, since_flush = 0;
+    for (; s < nrows && s < s_a; ++s) {
+        if (TMA && bulk->failed) break;
+        step(general, s);
+        if (++since_flush == kFlushRows) { flush(); since_flush = 0; }
+    }
+#pragma unroll 1
+    for (; s + SHINE_BWD_FAST_UNROLL <= s_b; s += SHINE_BWD_FAST_UNROLL) {
+        if (TMA && bulk->failed) break;
+        step(fast, s);
+        if (SHINE_BWD_FAST_UNROLL == 3) {
+            step(fast, s + 1);
+            step(fast, s + 2);
+        }
+        since_flush += SHINE_BWD_FAST_UNROLL;
+        if (since_flush >= kFlushRows) { flush(); since_flush = 0; }
+    }
+    for (; s < nrows; ++s) {
+        if (TMA && bulk->failed) break;
+        step(general, s);
+        if (++since_flush == kFlushRows) { flush(); since_flush = 0; }
     }
     acc[0] += partk;
 #pragma unroll
@@ -375,7 +471,19 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         acc[1 + i] += partw[i].x;
         acc[10 + i] += partw[i].y;
     }
-    cp_async_wait<0>();
+    if constexpr (TMA) {
+        if (bulk->failed) {
+            // Drain the copies issued but not waited for, with bounded waits, so that no bulk
+            // copy still writes this warp's shared memory when the kernel returns.
+            for (int s2 = last_done + 1; s2 <= last_issued; ++s2) {
+                const uint32_t q = seq0 + s2;
+                mbar_wait(bulk->bars + 8 * (q % NS), (q / NS) & 1u);
+            }
+        }
+        bulk->seq = seq0 + (uint32_t)nrows;  // every staged row was waited for and read
+    } else {
+        cp_async_wait<0>();
+    }
 }
 
 }  // namespace shine

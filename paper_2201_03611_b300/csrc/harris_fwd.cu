@@ -10,31 +10,45 @@ namespace shine {
 
 namespace {
 
-template <typename TI, typename TO, int NS, bool ALIGNED>
+template <typename TI, typename TO, int D, bool ALIGNED, bool TMA>
 __global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_kernel(FwdArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int NS = kFwdBulkStages;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kFwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
-    TI* ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
+    FwdBulk bulk;
+    bulk.seq = 0;
+    bulk.failed = false;
+    TI* ring = nullptr;
+    if constexpr (TMA) {
+        ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
+        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdThreads * NS * 12 * sizeof(TI)) + warp * NS;
+        bulk.bars = smem_u32(bars);
+        if (lane == 0)
+            for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+        mbar_init_fence();
+        __syncwarp();
+    }
     Params P;
     load_params(P, a.wx, a.wy, a.kappa);
-    // This warp's equal share of the (segment, row) units, walked segment by segment.
+    // This warp's share of the (segment, row) units, walked segment by segment.
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
     warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
-    while (lo < hi) {
+    while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
         const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
         const int xb = a.x0 + seg * kSegOut;
         const int x = xb - 4 + 4 * lane;
         const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W) || a.valid;
-        if (edge) fwd_strip<TI, TO, NS, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring);
-        else fwd_strip<TI, TO, NS, false, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring);
+        if (edge) fwd_strip<TI, TO, D, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+        else fwd_strip<TI, TO, D, false, ALIGNED, TMA, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring, &bulk);
         lo += r1 - r0;
     }
+    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
 }
 
 template <typename K>
@@ -50,13 +64,18 @@ int resident_warps(K kernel, int threads, size_t smem) {
 
 template <typename TI, typename TO>
 cudaError_t launch_fwd_t(FwdArgs a, cudaStream_t s) {
-    constexpr int NS = kFwdStages;
-    const size_t smem = (size_t)kFwdThreads * NS * 12 * sizeof(TI);
-    auto kern = a.aligned ? harris_fwd_kernel<TI, TO, NS, true> : harris_fwd_kernel<TI, TO, NS, false>;
+    constexpr int D = kFwdStages;
+    constexpr int NS = kFwdBulkStages;
+    const bool tma = a.tma && a.aligned;
+    const size_t smem = tma ? (size_t)kFwdThreads * NS * 12 * sizeof(TI) + (kFwdThreads / 32) * NS * 8 : 0;
+    auto kern = tma ? harris_fwd_kernel<TI, TO, D, true, true>
+                    : (a.aligned ? harris_fwd_kernel<TI, TO, D, true, false> : harris_fwd_kernel<TI, TO, D, false, false>);
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     if (units <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (tma) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int64_t t = resident_warps(kern, kFwdThreads, smem);
     t = std::min<int64_t>(t, std::max<int64_t>(1, units / kFwdMinRows));
     a.nwarps = (int)t;

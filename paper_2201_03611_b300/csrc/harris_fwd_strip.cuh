@@ -1,9 +1,10 @@
 // Forward strip: one warp computes R over one (column segment, row band) of one image.
 //
-// Rows are processed RB at a time: one wait for RB staged image rows, their gray rows and
-// Sobel rows, then the RB product/box/response rows. The RB rows' work is independent
-// (instruction-level parallelism for a warp that otherwise waits on shuffle and shared-memory
-// latency). HBM traffic is the image once and R once; nothing else leaves the registers.
+// Per output row y the warp takes one image row out of its register staging (loaded D rows
+// earlier, then refilled with the row D further down), makes its gray row, the Sobel row y+1,
+// the three product sums over rows y-1..y+1 (the slide2D + reduce of A4 done vertically in
+// registers first, then horizontally with two shuffles per plane) and R[y]. HBM traffic is the
+// image once and R once; nothing else leaves the registers.
 #pragma once
 
 #include "harris_common.cuh"
@@ -11,67 +12,110 @@
 
 namespace shine {
 
-template <typename TI, typename TO, int NS, bool EDGE, bool ALIGNED, int RB = kFwdRowsPerBlock>
+// Forward staging state of bulk (TMA) copies: see BulkState in harris_bwd_strip.cuh.
+struct FwdBulk {
+    uint32_t bars;  // shared address of this warp's NS barriers
+    uint32_t seq;   // rows staged by this warp so far
+    bool failed;    // a bounded wait gave up
+};
+
+// TMA = false: rows are staged in registers (D rows in flight). TMA = true (interior segments
+// with 16-byte aligned rows): lane 0 moves each row's whole 128-pixel segment into a ring of NS
+// shared-memory slots with one bulk copy completing on the slot's mbarrier; NS - 1 rows are in
+// flight without holding registers.
+template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED, bool TMA = false, int NS = 1>
 __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0,
-                                          int y1, TI* ring) {
-    // Staging: kFirst rows are put in flight up front; every block then reads RB rows and stages
-    // RB more. Before block b, rows up to 3 + RB (b + 1) + (kFirst - 4) have been issued while
-    // rows up to 3 + RB (b + 1) are needed, so waiting until at most kFirst - 4 groups are
-    // pending leaves that many rows in flight. Rows staged after a block's reads go to slots of
-    // rows consumed in earlier blocks (kFirst + 2 RB - 4 <= NS).
-    constexpr int kFirst = (NS + 4 - 2 * RB) < NS ? (NS + 4 - 2 * RB) : NS;
-    static_assert(kFirst - 4 >= RB, "the ring must hold at least one block in flight");
+                                          int y1, TI* ring = nullptr, FwdBulk* bulk = nullptr) {
     const int H = a.H, W = a.W;
-    PixelRows<TI, NS, EDGE, ALIGNED> rows(ring, static_cast<const TI*>(a.img), a.img_pitch, x, W);
-    const int nblocks = (y1 - y0 + RB - 1) / RB;
-    const int nrows = 4 + RB * nblocks;  // gray rows y0-2 .. y0+1+RB*nblocks (clamped)
-    const int r_first = y0 - 2;
+    const RegRows<TI, EDGE, ALIGNED> rows(static_cast<const TI*>(a.img), a.img_pitch, x, W);
+    const int r_first = y0 - 2;         // sequence row q is image row r_first + q (clamped)
+    const int nrows = y1 - y0 + 4;      // gray rows y0-2 .. y1+1
+    constexpr int kSlot = kLanes * 12;  // elements per shared-memory slot
+    constexpr uint32_t kBytes = kSegLoad * 3 * sizeof(TI);
+    const uint32_t seq0 = TMA ? bulk->seq : 0u;
+    int last_issued = -1, last_done = -1;
 
+    auto bulk_fetch = [&](int q) {
+        if constexpr (TMA) {
+            if (q < nrows) last_issued = q;
+            if (lane == 0 && q < nrows) {
+                const uint32_t n = seq0 + q, slot = n % NS, bar = bulk->bars + 8 * slot;
+                const TI* src = static_cast<const TI*>(a.img) + (int64_t)clampi(r_first + q, H) * a.img_pitch +
+                                (int64_t)(x - 4 * lane) * 3;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, kBytes);
+                bulk_copy_g2s(smem_u32(ring - lane * 12 + slot * kSlot), src, kBytes, bar);
+            }
+        }
+    };
+
+    RawRow<TI> buf[TMA ? 1 : D];  // register staging: buf[q % D] holds sequence row q until taken
+    if constexpr (TMA) {
 #pragma unroll
-    for (int q = 0; q < kFirst; ++q) {
-        if (q < nrows) rows.fetch(q % NS, clampi(r_first + q, H));
-        cp_async_commit();
+        for (int q = 0; q < NS - 1; ++q) bulk_fetch(q);
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) rows.load(clampi(r_first + d, H), buf[d]);
     }
-    int next = kFirst;  // next sequence row to stage
 
-    auto gray6 = [&](int q, float g6[6]) {
+    // Take sequence row q (from its register slot, refilled with row q + D; or from its shared
+    // slot, whose copy is then reissued for row q + NS - 1) and make the 6-wide gray row
+    // (clamped at the image border).
+    auto take = [&](int q, RawRow<TI>& slot, float g6[6]) {
         float v[12];
-        rows.read(q % NS, clampi(r_first + q, H), v);
+        if constexpr (TMA) {
+            const uint32_t n = seq0 + q, sl = n % NS;
+            const bool ok = __all_sync(kFull, mbar_wait(bulk->bars + 8 * sl, (n / NS) & 1u));
+            if (ok) last_done = q;
+            else bulk->failed = true;
+            const TI* src = ring + sl * kSlot;
+            if constexpr (sizeof(TI) == 4) {
+                const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float4 t = s4[i];
+                    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+                }
+            } else {
+                RawRow<TI> r;
+                const uint2* s2 = reinterpret_cast<const uint2*>(src);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) r.q[i] = s2[i];
+                RegRows<TI, EDGE, ALIGNED>::unpack(r, v);
+            }
+            __syncwarp();  // every lane has read the slot the next copy overwrites
+            if (ok) bulk_fetch(q + NS - 1);
+        } else {
+            RegRows<TI, EDGE, ALIGNED>::unpack(slot, v);
+            if (q + D < nrows) rows.load(clampi(r_first + q + D, H), slot);
+        }
         float c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = gray_of(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
         make_row6(c, g6);
         if constexpr (EDGE) clamp_row6(g6, x, W);
     };
-    auto stage_more = [&]() {
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-            if (next < nrows) rows.fetch(next % NS, clampi(r_first + next, H));
-            cp_async_commit();
-            ++next;
-        }
-    };
 
-    // g[0], g[1]: gray rows y, y+1 of the coming block; I[0], I[1]: Sobel rows y-1, y.
-    float g[RB + 2][6];
-    float2 I[RB + 2][4];
-    {
-        cp_async_wait<kFirst - 4>();  // sequence rows 0..3 landed
-        float g0[6], g1[6];
-        gray6(0, g0);
-        gray6(1, g1);
-        gray6(2, g[0]);
-        gray6(3, g[1]);
-        stage_more();
-        sobel(P, g0, g1, g[0], I[0]);  // row y0-1 (replaced by row y0 at the top border)
-        sobel(P, g1, g[0], g[1], I[1]);  // row y0
-    }
+    float g0[6], g1[6], g2[6];
+    float2 Ia[4], Ib[4], Ic[4];  // Sobel rows y-1, y, y+1
+    constexpr int DB = TMA ? 1 : D;
+    take(0, buf[0 % DB], g0);
+    take(1, buf[1 % DB], g1);
+    take(2, buf[2 % DB], g2);
+    sobel(P, g0, g1, g2, Ia);  // row y0-1 (replaced by row y0 at the top border)
+    take(3, buf[3 % DB], g0);
+    sobel(P, g1, g2, g0, Ib);  // row y0
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { float t = g1[i]; g1[i] = g0[i]; g0[i] = g2[i]; g2[i] = t; }
+    // now g0 = gray row y0, g1 = gray row y0 + 1 (g2 is scratch)
 
     TO* out = static_cast<TO*>(a.out);
     const bool producer = lane >= 1 && lane <= 30;
 
-    auto emit = [&](int y, const float2 Iu[4], const float2 Im[4], const float2 Id[4]) {
-        if (y >= y1) return;
+    auto step = [&](int q, RawRow<TI>& slot) {
+        const int y = y0 + q - 4;
+        take(q, slot, g2);             // gray row y+2
+        sobel(P, g0, g1, g2, Ic);      // row y+1 (replaced by row y at the bottom border)
         // A3 + A4: products summed over rows y-1, y, y+1, clamped at their own stage.
         float2 v2[4];
         float vxy[4];
@@ -79,12 +123,12 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
             float2 A[4], B[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                A[j] = (y == 0) ? Im[j] : Iu[j];
-                B[j] = (y == H - 1) ? Im[j] : Id[j];
+                A[j] = (y == 0) ? Ib[j] : Ia[j];
+                B[j] = (y == H - 1) ? Ib[j] : Ic[j];
             }
-            vertical_products(A, Im, B, v2, vxy);
+            vertical_products(A, Ib, B, v2, vxy);
         } else {
-            vertical_products(Iu, Im, Id, v2, vxy);
+            vertical_products(Ia, Ib, Ic, v2, vxy);
         }
         float2 s2[4];
         float sxy[4];
@@ -114,29 +158,31 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { Ia[j] = Ib[j]; Ib[j] = Ic[j]; }
     };
 
+    // Main loop: D steps per iteration so that every register staging slot index is a constant.
 #pragma unroll 1
-    for (int b = 0; b < nblocks; ++b) {
-        const int q = 4 + RB * b;  // first sequence row of this block (gray row y+2)
-        const int y = y0 + RB * b;
-        cp_async_wait<kFirst - 4>();  // sequence rows q .. q+RB-1 landed
+    for (int q0 = 4; q0 < nrows; q0 += DB) {
+        if (TMA && bulk->failed) break;
 #pragma unroll
-        for (int i = 0; i < RB; ++i) gray6(q + i, g[2 + i]);
-        stage_more();
-#pragma unroll
-        for (int i = 0; i < RB; ++i) sobel(P, g[i], g[i + 1], g[i + 2], I[2 + i]);  // rows y+1 ..
-#pragma unroll
-        for (int i = 0; i < RB; ++i) emit(y + i, I[i], I[i + 1], I[i + 2]);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) g[i][c] = g[RB + i][c];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) I[i][j] = I[RB + i][j];
-        }
+        for (int d = 0; d < DB; ++d)
+            if (q0 + d < nrows) step(q0 + d, buf[(4 + d) % DB]);
     }
-    cp_async_wait<0>();
+    if constexpr (TMA) {
+        if (bulk->failed) {
+            // Drain the copies issued but not waited for (bounded), so that no bulk copy still
+            // writes this warp's shared memory when the kernel returns.
+            for (int q = last_done + 1; q <= last_issued; ++q) {
+                const uint32_t n = seq0 + q;
+                mbar_wait(bulk->bars + 8 * (n % NS), (n / NS) & 1u);
+            }
+        }
+        bulk->seq = seq0 + (uint32_t)nrows;
+    }
 }
 
 }  // namespace shine

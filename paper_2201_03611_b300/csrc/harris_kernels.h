@@ -12,19 +12,25 @@ constexpr int kSegLoad = kLanes * kCols;       // 128 staged columns per warp se
 constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp segment
 // Compile-time tuning of the kernels (each has a default; the values are chosen by measurement).
 #ifndef SHINE_FWD_STAGES
-#define SHINE_FWD_STAGES 8        // staged image rows of the forward ring
+#define SHINE_FWD_STAGES 2        // image rows the forward keeps in flight (register staging)
 #endif
-#ifndef SHINE_FWD_ROWS
-#define SHINE_FWD_ROWS 2          // rows per forward block
+#ifndef SHINE_FWD_TMA
+#define SHINE_FWD_TMA 1           // forward interior segments staged by bulk copies
+#endif
+#ifndef SHINE_FWD_BULK_STAGES
+#define SHINE_FWD_BULK_STAGES 6   // shared-memory slots of the forward's bulk staging ring
 #endif
 #ifndef SHINE_FWD_MIN_BLOCKS
-#define SHINE_FWD_MIN_BLOCKS 1    // resident CTAs per SM the forward register budget must allow
+#define SHINE_FWD_MIN_BLOCKS 4    // resident CTAs per SM the forward register budget must allow
 #endif
 #ifndef SHINE_BWD_STAGES
-#define SHINE_BWD_STAGES 4        // staged rows of the backward ring
+#define SHINE_BWD_STAGES 8        // staged rows of the backward ring
 #endif
-#ifndef SHINE_BWD_UNROLL
-#define SHINE_BWD_UNROLL 1        // unrolling of the backward row loop
+#ifndef SHINE_BWD_FAST_UNROLL
+#define SHINE_BWD_FAST_UNROLL 1   // backward fast steps per loop iteration (1 or 3)
+#endif
+#ifndef SHINE_BWD_TMA
+#define SHINE_BWD_TMA 1           // backward interior segments staged by bulk copies
 #endif
 #ifndef SHINE_FWD_BAND_MAJOR
 #define SHINE_FWD_BAND_MAJOR 1    // forward: equal row bands across all segments
@@ -34,10 +40,10 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #endif
 constexpr int kFwdThreads = 128;  // 4 warps per CTA
 constexpr int kFwdStages = SHINE_FWD_STAGES;
-constexpr int kFwdRowsPerBlock = SHINE_FWD_ROWS;
+constexpr int kFwdBulkStages = SHINE_FWD_BULK_STAGES;
 constexpr int kBwdThreads = 128;
 constexpr int kBwdStages = SHINE_BWD_STAGES;
-constexpr int kBwdUnroll = SHINE_BWD_UNROLL;
+
 constexpr int kParamSlots = 19;   // d kappa, d Wx[9], d Wy[9]
 
 // Geometry shared by all kernels: which output region of the image a launch covers and how
@@ -92,6 +98,8 @@ struct FwdArgs : Geometry {
     const float* wy;
     int aligned;  // image rows can be staged with 16 / 8-byte copies
     int out_vec;  // output rows can be written with 16 / 8-byte stores
+    int tma;      // interior segments may use bulk (TMA) staging (16-byte aligned rows)
+    unsigned int* err;  // nonzero after a bounded wait gave up (nullable)
 };
 
 // The backward pass always covers every image pixel (its output is d img, H x W), so its
@@ -108,7 +116,9 @@ struct BwdArgs : Geometry {
     const float* kappa;
     const float* wx;
     const float* wy;
-    double* partials;  // [kParamSlots][nseg * nband]
+    double* partials;  // [kParamSlots][nwarps]
+    unsigned int* err; // nonzero after a bounded wait gave up (reset by the host before launch)
+    int tma;           // interior segments may use bulk (TMA) staging
     int aligned;       // image staging
     int g_aligned;     // cotangent staging (CLAMP with aligned pointer and pitch)
     int gimg_vec;      // d img rows can be written with 16 / 8-byte stores
@@ -125,6 +135,11 @@ cudaError_t launch_harris_bwd(BwdArgs a, int dt, int gout_dt, int max_warps, cud
 constexpr int kFwdMinRows = 16;  // minimum rows per warp slice
 constexpr int kBwdMinRows = 32;
 constexpr int kMaxWarpsPerSm = 64;
+constexpr size_t kWorkspaceHeader = 256;  // backward workspace: error word, then the partial sums
+// First output column of segment 0 (both passes): chosen so that every interior segment's
+// staged span (4 columns left of its output) starts on a 16-byte boundary for float32 and 16-bit
+// rows alike (120 * (s - 1) pixels), which bulk copies require.
+constexpr int kBwdSegmentOrigin = -116;
 // out[f] = sum over n partials[f * n + i] (fixed order, float64), f < kParamSlots; any out
 // pointer may be NULL.
 cudaError_t launch_finalize_params(const double* partials, int64_t n, float* gkappa, float* gwx,

@@ -20,12 +20,13 @@ namespace {
 // Partial-sum slots per parameter cotangent. The backward pass uses at most 64 warps per SM
 // (one slot each), so this covers any image on a GPU with up to 256 SMs.
 constexpr int64_t kNoAllocWarps = 16384;
-constexpr size_t kNoAllocBytes = (size_t)kParamSlots * kNoAllocWarps * sizeof(double);  // ~2.5 MB
+constexpr size_t kNoAllocBytes =
+    kWorkspaceHeader + (size_t)kParamSlots * kNoAllocWarps * sizeof(double);  // ~2.5 MB
 
 // Lives on every GPU that loads the library, until the process exits. In host code this
 // name is only a stand-in for the symbol, never a device address: the address is looked up
 // per device below.
-__device__ __align__(256) double g_bwd_partials[kParamSlots * kNoAllocWarps];
+__device__ __align__(256) double g_bwd_partials[kNoAllocBytes / sizeof(double)];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;

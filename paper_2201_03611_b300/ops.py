@@ -70,6 +70,14 @@ def bwd_workspace_bytes(h: int, w: int, border: str) -> int:
     return n.value
 
 
+def workspace_failed(workspace: torch.Tensor) -> bool:
+    """True when the last backward pass on this workspace gave up a bounded wait (results
+    invalid). Synchronises with the device."""
+    f = ctypes.c_int()
+    L.check(L.lib().shine_workspace_status(_ptr(workspace), ctypes.byref(f)), "shine_workspace_status")
+    return bool(f.value)
+
+
 def _row_pitch(t: torch.Tensor) -> int:
     return t.stride(0)
 

@@ -163,3 +163,15 @@ def test_autograd_function(shine):
     shine.harris(img2, 0.05, wxd.detach(), wyd.detach(), "valid").sum().backward()
     gi2 = cref.backward(img.detach().cpu(), torch.ones(41, 136), 0.05, wx, wy, "valid")[0]
     assert U.rel(U.host(img2.grad), gi2) <= U.TOL_GIMG
+
+
+def test_bounded_waits_report_no_failure(shine):
+    """Every wait of the staging pipeline is bounded; a normal run must report none gave up."""
+    from paper_2201_03611_b300.ops import bwd_workspace_bytes, workspace_failed
+    for (h, w) in ((517, 1030), (64, 124), (3, 5)):
+        img = wl.random_image(h, w, seed=1).cuda()
+        g = wl.random_cotangent(h, w, seed=2).cuda()
+        k, wx, wy = U.dev_params(0.04, *wl.random_weights(1))
+        ws = torch.empty(bwd_workspace_bytes(h, w, "clamp"), dtype=torch.uint8, device="cuda")
+        shine.pipeline_bwd(img, g, k, wx, wy, "clamp", workspace=ws)
+        assert not workspace_failed(ws)
