@@ -133,18 +133,28 @@ class ClockSampler:
 
 
 def _barrier_sync(world):
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def _max_over_ranks(v: float, world: int, device) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if world == 1:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dev = device if torch.distributed.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(pixels_per_rank_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job Gpixel/s: every rank processes its own replica (weak scaling), the time is the
+    slowest rank's."""
+    return world * pixels_per_rank_step * steps / (max_ms * 1e-3) / 1e9
 
 
 def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: int) -> dict:
@@ -210,7 +220,7 @@ def run_ours(args, world, rank, local) -> dict | None:
     fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
     px = size * size
-    value = world * px * K / (total_ms * 1e-3) / 1e9
+    value = job_throughput(px, K, world, total_ms)
 
     # end to end through the public API with host buffers: pinned host -> device, both passes,
     # device -> host of R, d img and the parameter cotangents, every step
@@ -278,7 +288,130 @@ def run_ours(args, world, rank, local) -> dict | None:
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(img_h, g_h, kappa, rows=args.cpu_rows)
+    if world == 1 and not args.no_extras:
+        del img, g, out, gimg, ws, img_pin, g_pin, out_pin, gimg_pin
+        torch.cuda.empty_cache()
+        extras = {"note": "other workloads, measured after the timed region; not part of value"}
+        extras["precision"] = precision_extra(S, device, size, reps=max(10, K // 10))
+        extras["batched"] = batched_extra(S, device, n=512, reps=20)
+        line["extras"] = extras
     return line
+
+
+def _time_ms(fn, reps: int, stream) -> float:
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _err_stats(got: torch.Tensor, ref) -> dict:
+    import numpy as np
+    g = got.detach().double().cpu().numpy().reshape(-1)
+    r = np.asarray(ref, np.float64).reshape(-1)
+    scale = max(np.abs(r).max(), 1e-300)
+    d = np.abs(g - r)
+    floor = np.maximum(np.abs(r), 1e-6 * scale)
+    return {"normwise_max": float(d.max() / scale), "normwise_mean": float(d.mean() / scale),
+            "pointwise_mean": float((d / floor).mean())}
+
+
+def precision_extra(S, device, size: int, reps: int) -> dict:
+    """The precision workload: bf16 / fp16 storage (float32 arithmetic), forward + backward of the
+    unsalted size x size image, timed like the main step; errors on sampled outputs against the
+    oracle on the quantised input, and (total error) against the oracle on the float32 input."""
+    from oracle import cref
+    out = {}
+    img32 = wl.random_image(size, size, seed=0)
+    g32 = wl.random_cotangent(size, size, seed=1)
+    wx, wy = wl.sobel_weights()
+    k = torch.tensor([wl.KAPPA], device=device)
+    dwx, dwy = wx.to(device), wy.to(device)
+    pts = wl.sample_points(size, size, 2000, seed=7)
+    ref32 = cref.forward_points(img32, wl.KAPPA, wx, wy, "clamp", pts)
+    for name in ("bf16", "f16"):
+        dt = wl.storage_dtype(name)
+        img_q = img32.to(dt)
+        img = img_q.to(device)
+        g = g32.to(dt).to(device)
+        o = torch.empty(size, size, device=device, dtype=dt)
+        gi = torch.empty_like(img)
+        ws = torch.empty(S.bwd_workspace_bytes(size, size, "clamp"), dtype=torch.uint8, device=device)
+        stream = torch.cuda.current_stream(device)
+        fwd = lambda: S.pipeline_fwd(img, k, dwx, dwy, "clamp", out=o)
+        bwd = lambda: S.pipeline_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, grad_img=gi)
+        for _ in range(3):
+            fwd(); bwd()
+        torch.cuda.synchronize()
+        t_f = _time_ms(fwd, reps, stream)
+        t_b = _time_ms(bwd, reps, stream)
+        px = size * size
+        ref_q = cref.forward_points(img_q, wl.KAPPA, wx, wy, "clamp", pts)
+        got = o[pts[:, 0].to(device), pts[:, 1].to(device)].float().cpu()
+        o32 = S.pipeline_fwd(img, k, dwx, dwy, "clamp", out_dtype=torch.float32)
+        got32 = o32[pts[:, 0].to(device), pts[:, 1].to(device)].cpu()
+        out[name] = {
+            "fwd_ms": t_f, "bwd_ms": t_b, "step_gpix_s": px / ((t_f + t_b) * 1e-3) / 1e9,
+            "fwd_frac_of_measured_hbm": 8 * px / (t_f * 1e-3) / 1e9 / _peaks()[0],
+            "bwd_frac_of_measured_hbm": 14 * px / (t_b * 1e-3) / 1e9 / _peaks()[0],
+            "R_err_vs_oracle_on_quantised_input": _err_stats(got, ref_q),
+            "R_f32_output_err_vs_oracle_on_quantised_input": _err_stats(got32, ref_q),
+            "R_err_vs_oracle_on_f32_input": _err_stats(got, ref32),
+            "sample": f"{pts.shape[0]} outputs (random, corners, border bands)"}
+        del img, g, o, gi, ws, o32
+    return out
+
+
+def batched_extra(S, device, n: int, reps: int) -> dict:
+    """The uneven batch: n images, bf16 storage, forward + backward fused in one persistent
+    launch captured in a CUDA graph, against a loop of per-image fused launches."""
+    b = wl.batch_512(n=n)
+    imgs = [t.to(device) for t in b["imgs"]]
+    gouts = [t.to(device) for t in b["ws"]]
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    px = sum(h * w for h, w in shapes)
+    outs = [torch.empty(h, w, dtype=imgs[0].dtype, device=device) for h, w in shapes]
+    gimgs = [torch.empty_like(t) for t in imgs]
+    kappa = b["kappa"].to(device)
+    wx, wy = [t.to(device) for t in wl.sobel_weights()]
+    cache = os.path.join(ROOT, "paper_2201_03611_b300", "tune_cache.txt")
+    plan = S.BatchedPlan(shapes, imgs[0].dtype, "clamp", fwd_bwd=True,
+                         tune_cache=cache if os.path.exists(cache) else None)
+    descs = plan.bind(imgs, outs, gouts, gimgs)
+    ws = plan.new_workspace(device)
+    gk = torch.empty(n, device=device)
+    gwx, gwy = torch.empty(3, 3, device=device), torch.empty(3, 3, device=device)
+    side = torch.cuda.Stream(device)
+    side.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(side):
+        plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws)
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(device)
+    for _ in range(3):
+        graph.replay()
+    t_graph = _time_ms(graph.replay, reps, stream)
+    wss = [torch.empty(S.bwd_workspace_bytes(h, w, "clamp"), dtype=torch.uint8, device=device) for h, w in shapes]
+    kap = [kappa[i:i + 1] for i in range(n)]
+
+    def loop():
+        for i in range(n):
+            S.pipeline_fwd_bwd(imgs[i], gouts[i], kap[i], wx, wy, "clamp", workspace=wss[i], out=outs[i],
+                               grad_img=gimgs[i])
+    loop()
+    torch.cuda.synchronize()
+    t_loop = _time_ms(loop, max(1, reps // 4), stream)
+    return {"images": n, "pixels": px, "dtype": "bf16", "graph_ms": t_graph, "loop_ms": t_loop,
+            "graph_gpix_s": px / (t_graph * 1e-3) / 1e9, "loop_gpix_s": px / (t_loop * 1e-3) / 1e9,
+            "speedup_vs_per_image_loop": t_loop / t_graph,
+            "graph_frac_of_measured_hbm": 16 * px / (t_graph * 1e-3) / 1e9 / _peaks()[0],
+            "workspace_bytes": plan.workspace_bytes, "tuned": os.path.exists(cache)}
 
 
 def run_reference(args, world, rank) -> dict | None:
@@ -322,6 +455,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=2048)
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -98,12 +98,14 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
 
     float g0[6], g1[6], g2[6];
     float2 Ia[4], Ib[4], Ic[4];  // Sobel rows y-1, y, y+1
-    constexpr int DB = TMA ? 1 : D;
-    take(0, buf[0 % DB], g0);
-    take(1, buf[1 % DB], g1);
-    take(2, buf[2 % DB], g2);
+    // Steps per main-loop iteration: D for register staging (constant slot indices); for bulk
+    // staging kFwdUnroll, so that the 3-row gray and 2-row Sobel windows rotate by renaming.
+    constexpr int DB = TMA ? kFwdUnroll : D;
+    take(0, buf[TMA ? 0 : 0 % DB], g0);
+    take(1, buf[TMA ? 0 : 1 % DB], g1);
+    take(2, buf[TMA ? 0 : 2 % DB], g2);
     sobel(P, g0, g1, g2, Ia);  // row y0-1 (replaced by row y0 at the top border)
-    take(3, buf[3 % DB], g0);
+    take(3, buf[TMA ? 0 : 3 % DB], g0);
     sobel(P, g1, g2, g0, Ib);  // row y0
 #pragma unroll
     for (int i = 0; i < 6; ++i) { float t = g1[i]; g1[i] = g0[i]; g0[i] = g2[i]; g2[i] = t; }
@@ -170,7 +172,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
         if (TMA && bulk->failed) break;
 #pragma unroll
         for (int d = 0; d < DB; ++d)
-            if (q0 + d < nrows) step(q0 + d, buf[(4 + d) % DB]);
+            if (q0 + d < nrows) step(q0 + d, buf[TMA ? 0 : (4 + d) % DB]);
     }
     if constexpr (TMA) {
         if (bulk->failed) {
