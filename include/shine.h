@@ -123,6 +123,32 @@ SHINE_API shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W,
                                 float* grad_wy, void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Forward and backward of an image held in HOST memory: uploads, kernels and downloads are cut
+ * into nbands row bands and overlapped on the library's own streams (band b's kernels run once
+ * band b+1, holding its halo rows, has arrived), so the call costs about one transfer direction
+ * instead of the sum of both. Results equal those of shine_pipeline_fwd + shine_pipeline_bwd.
+ *   img_h, gout_h          host inputs, dense rows (pitch 3W / W_out elements); pinned memory
+ *                          is needed for the copies to overlap
+ *   out_h, gimg_h          host outputs (dense; each nullable)
+ *   kappa, wx, wy          device parameters
+ *   grad_params            device float32 [19]: d kappa, d Wx[9], d Wy[9] (nullable)
+ *   dev_img, dev_gout, dev_out, dev_gimg
+ *                          device buffers of the full sizes (dense, 16-byte aligned)
+ *   workspace              >= shine_pipeline_host_workspace() bytes of device memory
+ *   nbands                 1..64, and H >= 8 * nbands
+ * The caller's stream waits for all of it (copies included): synchronise that stream before
+ * reading the host outputs. One call at a time per device.
+ */
+SHINE_API shine_status shine_pipeline_host_workspace(int64_t H, int64_t W, shine_border border,
+                                          int32_t nbands, size_t* bytes);
+SHINE_API shine_status shine_pipeline_host(const void* img_h, const void* gout_h, void* out_h,
+                                 void* gimg_h, int64_t H, int64_t W, shine_dtype dt,
+                                 shine_border border, const float* kappa, const float* wx,
+                                 const float* wy, float* grad_params, void* dev_img,
+                                 void* dev_gout, void* dev_out, void* dev_gimg, void* workspace,
+                                 size_t ws_bytes, int32_t nbands, void* stream);
+
+/*
  * Backward pass that allocates nothing, for callers that cannot allocate device memory (a
  * plug-in handed only its input and output buffers, a real-time loop that forbids allocation
  * after start-up, code inside a framework that owns all device memory). The paper has no

@@ -190,6 +190,8 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     a.kappa = kappa; a.wx = wx; a.wy = wy;
     a.err = static_cast<unsigned int*>(workspace);
     a.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + kWorkspaceHeader);
+    a.pstride = 0;
+    a.poffset = 0;
     const size_t chunk = si == 4 ? 16 : 8;
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.g_aligned = border == SHINE_CLAMP && aligned_to(grad_out, 4 * sg) && ((size_t)gout_pitch * sg) % (4 * sg) == 0;

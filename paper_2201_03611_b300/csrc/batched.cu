@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
             a.gimg = d.grad_img; a.gimg_pitch = d.gimg_pitch;
             a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
             a.partials = nullptr;
+            a.pstride = 0;
+            a.poffset = 0;
             a.err = nullptr;
             a.tma = 0;
             a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);

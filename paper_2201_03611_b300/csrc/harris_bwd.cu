@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
         double v = producer ? (double)acc[i] : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (lane == 0) a.partials[(int64_t)i * a.nwarps + gw] = v;
+        if (lane == 0) a.partials[(int64_t)i * (a.pstride ? a.pstride : a.nwarps) + a.poffset + gw] = v;
     }
 }
 

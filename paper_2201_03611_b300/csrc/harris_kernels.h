@@ -120,7 +120,9 @@ struct BwdArgs : Geometry {
     const float* kappa;
     const float* wx;
     const float* wy;
-    double* partials;  // [kParamSlots][nwarps]
+    double* partials;  // slot i of warp w at partials[i * pstride + poffset + w]
+    int64_t pstride;   // 0: nwarps (one launch owns the partials)
+    int64_t poffset;
     unsigned int* err; // nonzero after a bounded wait gave up (reset by the host before launch)
     int tma;           // interior segments may use bulk (TMA) staging
     int aligned;       // image staging

@@ -156,6 +156,29 @@ def pipeline_fwd_bwd(img, grad_out, kappa, wx, wy, border: str = "clamp", need_i
     return out, gimg, gk, gwx, gwy
 
 
+def host_workspace_bytes(h: int, w: int, border: str, nbands: int) -> int:
+    n = ctypes.c_size_t()
+    L.check(L.lib().shine_pipeline_host_workspace(h, w, border_code(border), nbands, ctypes.byref(n)),
+            "shine_pipeline_host_workspace")
+    return n.value
+
+
+def pipeline_host(img_h, g_h, kappa, wx, wy, dev_img, dev_g, dev_out, dev_gimg, workspace, out_h=None,
+                  gimg_h=None, grad_params=None, border: str = "clamp", nbands: int = 16) -> None:
+    """Forward + backward of a host (pinned) image with band-pipelined copies
+    (shine_pipeline_host). Enqueues on the current stream; synchronise before reading the host
+    outputs."""
+    h, w = img_h.shape[0], img_h.shape[1]
+    for t in (img_h, g_h, out_h, gimg_h):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError("host buffers must be contiguous CPU tensors (pinned for overlap)")
+    L.check(L.lib().shine_pipeline_host(_ptr(img_h), _ptr(g_h), _ptr(out_h), _ptr(gimg_h), h, w,
+                                        dtype_code(img_h.dtype), border_code(border), _ptr(kappa), _ptr(wx),
+                                        _ptr(wy), _ptr(grad_params), _ptr(dev_img), _ptr(dev_g), _ptr(dev_out),
+                                        _ptr(dev_gimg), _ptr(workspace), workspace.numel(), nbands,
+                                        _stream(dev_img.device)), "shine_pipeline_host")
+
+
 def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
     if isinstance(v, torch.Tensor):
         return v

@@ -175,3 +175,36 @@ def test_bounded_waits_report_no_failure(shine):
         ws = torch.empty(bwd_workspace_bytes(h, w, "clamp"), dtype=torch.uint8, device="cuda")
         shine.pipeline_bwd(img, g, k, wx, wy, "clamp", workspace=ws)
         assert not workspace_failed(ws)
+
+
+@pytest.mark.parametrize("shape,border,dtype,nbands", [((203, 517), "clamp", torch.float32, 16),
+                                                       ((203, 517), "valid", torch.float32, 3),
+                                                       ((96, 250), "clamp", torch.bfloat16, 5),
+                                                       ((64, 130), "clamp", torch.float32, 1)])
+def test_host_pipeline_matches_device_calls(shine, shape, border, dtype, nbands):
+    """shine_pipeline_host (host buffers, band-pipelined copies) gives the device calls' R and
+    d img bit for bit, and the same parameter cotangents within the summation bound."""
+    from paper_2201_03611_b300 import ops
+    h, w = shape
+    ho, wo = shine.output_shape(h, w, border)
+    img_h = wl.random_image(h, w, seed=31).to(dtype).pin_memory()
+    g_h = wl.random_cotangent(ho, wo, seed=32).to(dtype).pin_memory()
+    k, wx, wy = U.dev_params(0.05, *wl.random_weights(31))
+    dev_img = torch.empty(h, w, 3, dtype=dtype, device="cuda")
+    dev_g = torch.empty(ho, wo, dtype=dtype, device="cuda")
+    dev_out = torch.empty(ho, wo, dtype=dtype, device="cuda")
+    dev_gimg = torch.empty(h, w, 3, dtype=dtype, device="cuda")
+    out_h = torch.empty(ho, wo, dtype=dtype).pin_memory()
+    gimg_h = torch.empty(h, w, 3, dtype=dtype).pin_memory()
+    par = torch.empty(19, device="cuda")
+    ws = torch.empty(ops.host_workspace_bytes(h, w, border, nbands), dtype=torch.uint8, device="cuda")
+    ops.pipeline_host(img_h, g_h, k, wx, wy, dev_img, dev_g, dev_out, dev_gimg, ws, out_h=out_h, gimg_h=gimg_h,
+                      grad_params=par, border=border, nbands=nbands)
+    torch.cuda.synchronize()
+    img, g = img_h.cuda(), g_h.cuda()
+    r = shine.pipeline_fwd(img, k, wx, wy, border)
+    gi, gk, gwx, gwy = shine.pipeline_bwd(img, g, k, wx, wy, border)
+    assert torch.equal(out_h, r.cpu())
+    assert torch.equal(gimg_h, gi.cpu())
+    ref = cref.backward(img_h, g_h, 0.05, wx.cpu(), wy.cpu(), border, with_abs=True)
+    U.assert_params((par[0:1], par[1:10].reshape(3, 3), par[10:19].reshape(3, 3)), ref[1:])
