@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_
         const int x = xb - 4 + 4 * lane;
         const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W) || a.valid;
         if (edge) fwd_strip<TI, TO, D, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
-        else fwd_strip<TI, TO, D, false, ALIGNED, TMA, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring, &bulk);
+        else if constexpr (TMA) fwd_strip_bulk<TI, TO, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring, bulk);
+        else fwd_strip<TI, TO, D, false, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
         lo += r1 - r0;
     }
     if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
@@ -66,7 +67,7 @@ template <typename TI, typename TO>
 cudaError_t launch_fwd_t(FwdArgs a, cudaStream_t s) {
     constexpr int D = kFwdStages;
     constexpr int NS = kFwdBulkStages;
-    const bool tma = a.tma && a.aligned;
+    const bool tma = a.tma && a.aligned && a.out_vec;  // the bulk strips store R with vector stores
     const size_t smem = tma ? (size_t)kFwdThreads * NS * 12 * sizeof(TI) + (kFwdThreads / 32) * NS * 8 : 0;
     auto kern = tma ? harris_fwd_kernel<TI, TO, D, true, true>
                     : (a.aligned ? harris_fwd_kernel<TI, TO, D, true, false> : harris_fwd_kernel<TI, TO, D, false, false>);

@@ -1,10 +1,10 @@
 // Forward strip: one warp computes R over one (column segment, row band) of one image.
 //
-// Per output row y the warp takes one image row out of its register staging (loaded D rows
-// earlier, then refilled with the row D further down), makes its gray row, the Sobel row y+1,
-// the three product sums over rows y-1..y+1 (the slide2D + reduce of A4 done vertically in
-// registers first, then horizontally with two shuffles per plane) and R[y]. HBM traffic is the
-// image once and R once; nothing else leaves the registers.
+// Per output row y the warp takes one image row out of its staging (loaded several rows
+// earlier), makes its gray row, the Sobel row y+1, the three product sums over rows y-1..y+1
+// (the slide2D + reduce of A4 done vertically in registers first, then horizontally with two
+// shuffles per plane) and R[y]. HBM traffic is the image once and R once; nothing else leaves
+// the registers.
 #pragma once
 
 #include "harris_common.cuh"
@@ -12,179 +12,197 @@
 
 namespace shine {
 
-// Forward staging state of bulk (TMA) copies: see BulkState in harris_bwd_strip.cuh.
+// Forward staging state of bulk (TMA) copies, carried by a warp from strip to strip.
 struct FwdBulk {
     uint32_t bars;  // shared address of this warp's NS barriers
-    uint32_t seq;   // rows staged by this warp so far
+    uint32_t seq;   // rows staged by this warp so far (row n sits in slot n % NS)
     bool failed;    // a bounded wait gave up
 };
 
-// TMA = false: rows are staged in registers (D rows in flight). TMA = true (interior segments
-// with 16-byte aligned rows): lane 0 moves each row's whole 128-pixel segment into a ring of NS
-// shared-memory slots with one bulk copy completing on the slot's mbarrier; NS - 1 rows are in
-// flight without holding registers.
-template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED, bool TMA = false, int NS = 1>
-__device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0,
-                                          int y1, TI* ring = nullptr, FwdBulk* bulk = nullptr) {
+// The 6-wide gray row (clamped at the image border on EDGE warps) of the lane's 12 channel values.
+template <bool EDGE>
+__device__ __forceinline__ void gray_row(const float v[12], float g6[6], int x, int W) {
+    float c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[j] = gray_of(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
+    make_row6(c, g6);
+    if constexpr (EDGE) clamp_row6(g6, x, W);
+}
+
+template <typename TO>
+__device__ __forceinline__ void store4(TO* p, const float R[4]) {
+    if constexpr (sizeof(TO) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(R[0], R[1], R[2], R[3]);
+    } else {
+        TO o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = Conv<TO>::st(R[j]);
+        *reinterpret_cast<uint2*>(p) = *reinterpret_cast<uint2*>(o);
+    }
+}
+
+// The strip walk shared by both staging methods: y0 .. y1-1 are the output rows, take(q, k,
+// g6) delivers sequence row q (image row y0 - 2 + q, clamped) as a gray row (k = q mod D, a
+// constant in unrolled code), store(y, R) writes R[y], and go() is false once the staging has
+// failed. Per output row: one gray row in, one Sobel row completed, one row of product sums
+// completed, the horizontal box sums, the response. The running sums are updated in place, so
+// the loop keeps no window of rows that would have to be shifted.
+template <bool EDGE, int D, typename Take, typename Store, typename Go>
+__device__ __forceinline__ void fwd_strip_core(const Params& P, int x, int W, int H, int y0, int y1, Take&& take,
+                                               Store&& store, Go&& go) {
+    StripRun st;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) st.P1[j] = st.P2[j] = make_float2(0.0f, 0.0f);
+    float g[6];
+    take(0, 0 % D, g);
+    push_gray(P, g, st);
+    take(1, 1 % D, g);
+    push_gray(P, g, st);
+    take(2, 2 % D, g);
+    push_gray(P, g, st);  // S = Sobel row y0-1
+    square_S(st);
+    take(3, 3 % D, g);
+    push_gray(P, g, st);  // S = Sobel row y0
+    if (y0 == 0) square_S(st);  // the product row above the image is the clamped copy of row 0
+    add_S(st);
+    square_S(st);
+#pragma unroll 1
+    for (int y = y0; y < y1; y += D) {
+        if (!go()) break;
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            const int yy = y + u;
+            if (u == 0 || yy < y1) {
+                take(yy - y0 + 4, (4 + u) % D, g);  // gray row yy+2
+                // S = Sobel row yy+1; at the bottom image row S stays at row yy, the clamped
+                // row below it at the product stage.
+                if (yy != H - 1) push_gray(P, g, st);
+                float2 v2[4];
+                float vxy[4];
+                push_products(st, v2, vxy);
+                float2 s2[4];
+                float sxy[4];
+                horizontal_box<EDGE>(v2, s2, x, W);
+                horizontal_box<EDGE>(vxy, sxy, x, W);
+                float R[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) R[j] = response(s2[j].x, sxy[j], s2[j].y, P.kappa);
+                store(yy, R);
+            }
+        }
+    }
+}
+
+// Strip with register staging (D rows in flight): every segment kind, any alignment.
+template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED>
+__device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
     const int H = a.H, W = a.W;
     const RegRows<TI, EDGE, ALIGNED> rows(static_cast<const TI*>(a.img), a.img_pitch, x, W);
-    const int r_first = y0 - 2;         // sequence row q is image row r_first + q (clamped)
-    const int nrows = y1 - y0 + 4;      // gray rows y0-2 .. y1+1
-    constexpr int kSlot = kLanes * 12;  // elements per shared-memory slot
-    constexpr uint32_t kBytes = kSegLoad * 3 * sizeof(TI);
-    const uint32_t seq0 = TMA ? bulk->seq : 0u;
-    int last_issued = -1, last_done = -1;
-
-    auto bulk_fetch = [&](int q) {
-        if constexpr (TMA) {
-            if (q < nrows) last_issued = q;
-            if (lane == 0 && q < nrows) {
-                const uint32_t n = seq0 + q, slot = n % NS, bar = bulk->bars + 8 * slot;
-                const TI* src = static_cast<const TI*>(a.img) + (int64_t)clampi(r_first + q, H) * a.img_pitch +
-                                (int64_t)(x - 4 * lane) * 3;
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, kBytes);
-                bulk_copy_g2s(smem_u32(ring - lane * 12 + slot * kSlot), src, kBytes, bar);
-            }
-        }
-    };
-
-    RawRow<TI> buf[TMA ? 1 : D];  // register staging: buf[q % D] holds sequence row q until taken
-    if constexpr (TMA) {
+    const int r_first = y0 - 2;     // sequence row q is image row r_first + q (clamped)
+    const int nrows = y1 - y0 + 4;  // gray rows y0-2 .. y1+1
+    RawRow<TI> buf[D];              // buf[q % D] holds sequence row q until taken
 #pragma unroll
-        for (int q = 0; q < NS - 1; ++q) bulk_fetch(q);
-    } else {
-#pragma unroll
-        for (int d = 0; d < D; ++d) rows.load(clampi(r_first + d, H), buf[d]);
-    }
-
-    // Take sequence row q (from its register slot, refilled with row q + D; or from its shared
-    // slot, whose copy is then reissued for row q + NS - 1) and make the 6-wide gray row
-    // (clamped at the image border).
-    auto take = [&](int q, RawRow<TI>& slot, float g6[6]) {
+    for (int d = 0; d < D; ++d) rows.load(clampi(r_first + d, H), buf[d]);
+    auto take = [&](int q, int k, float g6[6]) {
         float v[12];
-        if constexpr (TMA) {
-            const uint32_t n = seq0 + q, sl = n % NS;
-            const bool ok = __all_sync(kFull, mbar_wait(bulk->bars + 8 * sl, (n / NS) & 1u));
-            if (ok) last_done = q;
-            else bulk->failed = true;
-            const TI* src = ring + sl * kSlot;
-            if constexpr (sizeof(TI) == 4) {
-                const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float4 t = s4[i];
-                    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-                }
-            } else {
-                RawRow<TI> r;
-                const uint2* s2 = reinterpret_cast<const uint2*>(src);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) r.q[i] = s2[i];
-                RegRows<TI, EDGE, ALIGNED>::unpack(r, v);
-            }
-            __syncwarp();  // every lane has read the slot the next copy overwrites
-            if (ok) bulk_fetch(q + NS - 1);
-        } else {
-            RegRows<TI, EDGE, ALIGNED>::unpack(slot, v);
-            if (q + D < nrows) rows.load(clampi(r_first + q + D, H), slot);
-        }
-        float c[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) c[j] = gray_of(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
-        make_row6(c, g6);
-        if constexpr (EDGE) clamp_row6(g6, x, W);
+        RegRows<TI, EDGE, ALIGNED>::unpack(buf[k], v);
+        if (q + D < nrows) rows.load(clampi(r_first + q + D, H), buf[k]);
+        gray_row<EDGE>(v, g6, x, W);
     };
-
-    float g0[6], g1[6], g2[6];
-    float2 Ia[4], Ib[4], Ic[4];  // Sobel rows y-1, y, y+1
-    // Steps per main-loop iteration: D for register staging (constant slot indices); for bulk
-    // staging kFwdUnroll, so that the 3-row gray and 2-row Sobel windows rotate by renaming.
-    constexpr int DB = TMA ? kFwdUnroll : D;
-    take(0, buf[TMA ? 0 : 0 % DB], g0);
-    take(1, buf[TMA ? 0 : 1 % DB], g1);
-    take(2, buf[TMA ? 0 : 2 % DB], g2);
-    sobel(P, g0, g1, g2, Ia);  // row y0-1 (replaced by row y0 at the top border)
-    take(3, buf[TMA ? 0 : 3 % DB], g0);
-    sobel(P, g1, g2, g0, Ib);  // row y0
-#pragma unroll
-    for (int i = 0; i < 6; ++i) { float t = g1[i]; g1[i] = g0[i]; g0[i] = g2[i]; g2[i] = t; }
-    // now g0 = gray row y0, g1 = gray row y0 + 1 (g2 is scratch)
-
     TO* out = static_cast<TO*>(a.out);
     const bool producer = lane >= 1 && lane <= 30;
-
-    auto step = [&](int q, RawRow<TI>& slot) {
-        const int y = y0 + q - 4;
-        take(q, slot, g2);             // gray row y+2
-        sobel(P, g0, g1, g2, Ic);      // row y+1 (replaced by row y at the bottom border)
-        // A3 + A4: products summed over rows y-1, y, y+1, clamped at their own stage.
-        float2 v2[4];
-        float vxy[4];
-        if (y == 0 || y == H - 1) {
-            float2 A[4], B[4];
+    auto store = [&](int y, const float R[4]) {
+        if (!producer) return;
+        TO* orow = out + (int64_t)(y - a.oy) * a.out_pitch;
+        if (!EDGE && a.out_vec) {
+            store4(orow + x, R);
+        } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                A[j] = (y == 0) ? Ib[j] : Ia[j];
-                B[j] = (y == H - 1) ? Ib[j] : Ic[j];
-            }
-            vertical_products(A, Ib, B, v2, vxy);
-        } else {
-            vertical_products(Ia, Ib, Ic, v2, vxy);
-        }
-        float2 s2[4];
-        float sxy[4];
-        horizontal_box<EDGE>(v2, s2, x, W);
-        horizontal_box<EDGE>(vxy, sxy, x, W);
-        // A5
-        float R[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) R[j] = response(s2[j].x, sxy[j], s2[j].y, P.kappa);
-        if (producer) {
-            const int yo = y - a.oy;
-            TO* orow = out + (int64_t)yo * a.out_pitch;
-            if (!EDGE && a.out_vec) {
-                if constexpr (sizeof(TO) == 4) {
-                    *reinterpret_cast<float4*>(orow + x) = make_float4(R[0], R[1], R[2], R[3]);
-                } else {
-                    TO o[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = Conv<TO>::st(R[j]);
-                    *reinterpret_cast<uint2*>(orow + x) = *reinterpret_cast<uint2*>(o);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    int c = x + j;
-                    if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
-                }
+                const int c = x + j;
+                if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
             }
         }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { Ia[j] = Ib[j]; Ib[j] = Ic[j]; }
     };
+    fwd_strip_core<EDGE, D>(P, x, W, H, y0, y1, take, store, [] { return true; });
+}
 
-    // Main loop: D steps per iteration so that every register staging slot index is a constant.
-#pragma unroll 1
-    for (int q0 = 4; q0 < nrows; q0 += DB) {
-        if (TMA && bulk->failed) break;
-#pragma unroll
-        for (int d = 0; d < DB; ++d)
-            if (q0 + d < nrows) step(q0 + d, buf[TMA ? 0 : (4 + d) % DB]);
-    }
-    if constexpr (TMA) {
-        if (bulk->failed) {
-            // Drain the copies issued but not waited for (bounded), so that no bulk copy still
-            // writes this warp's shared memory when the kernel returns.
-            for (int q = last_done + 1; q <= last_issued; ++q) {
-                const uint32_t n = seq0 + q;
-                mbar_wait(bulk->bars + 8 * (n % NS), (n / NS) & 1u);
-            }
+// Strip of an interior segment with 16-byte aligned rows, staged by bulk (TMA) copies: lane 0
+// moves each row's whole 128-pixel segment into a ring of NS shared-memory slots with one copy
+// completing on the slot's mbarrier, so NS rows are in flight without holding registers. The
+// ring position and the row pointers are strength-reduced: per row the warp does the barrier
+// wait, three shared loads, one copy issue and the arithmetic.
+template <typename TI, typename TO, int NS>
+__device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                               const TI* ring, FwdBulk& bulk) {
+    const int H = a.H;
+    const int nrows = y1 - y0 + 4;  // gray rows y0-2 .. y1+1 (sequence rows 0 .. nrows-1)
+    constexpr int kSlot = kLanes * 12;  // elements per slot
+    constexpr uint32_t kBytes = kSegLoad * 3 * sizeof(TI);
+    const TI* seg = static_cast<const TI*>(a.img) + (int64_t)(x - 4 * lane) * 3;
+    const uint32_t ring0 = smem_u32(ring - lane * 12);  // slot 0 of the warp's ring
+    const uint32_t lane_ring = smem_u32(ring);          // this lane's 12 elements of slot 0
+    const uint32_t seq0 = bulk.seq;
+    uint32_t slot = seq0 % NS, phase = (seq0 / NS) & 1u;  // next row to take
+    int fq = 0;  // next sequence row to fetch; it goes to the slot of row fq - NS
+    uint32_t fslot = slot;
+    int tq = 0, failed_q = 0;  // rows taken; the first row whose wait gave up
+
+    auto fetch = [&]() {
+        if (lane == 0) {
+            const TI* src = seg + (int64_t)clampi(y0 - 2 + fq, H) * a.img_pitch;
+            const uint32_t bar = bulk.bars + 8 * fslot;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, kBytes);
+            bulk_copy_g2s(ring0 + fslot * (kSlot * (uint32_t)sizeof(TI)), src, kBytes, bar);
         }
-        bulk->seq = seq0 + (uint32_t)nrows;
+        ++fq;
+        fslot = fslot + 1 == NS ? 0 : fslot + 1;
+    };
+#pragma unroll 1
+    for (int i = 0; i < NS && fq < nrows; ++i) fetch();
+
+    // Take the next row as a gray row; its slot is then refilled with the row NS further on.
+    auto take = [&](int, int, float g6[6]) {
+        const bool ok = warp_mbar_wait(bulk.bars + 8 * slot, phase, lane);
+        if (!ok && !bulk.failed) { bulk.failed = true; failed_q = tq; }
+        ++tq;
+        float v[12];
+        const uint32_t src = lane_ring + slot * (kSlot * (uint32_t)sizeof(TI));
+        if constexpr (sizeof(TI) == 4) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float4 t = lds128(src + 16 * i);
+                v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+            }
+        } else {
+            RawRow<TI> r;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) r.q[i] = lds64(src + 8 * i);
+            RegRows<TI, false, true>::unpack(r, v);
+        }
+        __syncwarp();  // every lane has read the slot before the copy that overwrites it
+        if (!bulk.failed && fq < nrows) fetch();
+        if (++slot == NS) { slot = 0; phase ^= 1u; }
+        gray_row<false>(v, g6, x, 0);
+    };
+    TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
+    const int64_t opitch = a.out_pitch;
+    const bool producer = lane >= 1 && lane <= 30;
+    auto store = [&](int, const float R[4]) {
+        if (producer) store4(orow, R);
+        orow += opitch;
+    };
+    fwd_strip_core<false, 1>(P, x, 0, H, y0, y1, take, store, [&] { return !bulk.failed; });
+    if (bulk.failed) {
+        // Drain the copies issued but not seen complete (bounded waits), so that no bulk copy
+        // still writes this warp's shared memory when the kernel returns.
+        for (int q = failed_q; q < fq; ++q) {
+            const uint32_t n = seq0 + (uint32_t)q;
+            mbar_wait(bulk.bars + 8 * (n % NS), (n / NS) & 1u);
+        }
     }
+    bulk.seq = seq0 + (uint32_t)nrows;
 }
 
 }  // namespace shine

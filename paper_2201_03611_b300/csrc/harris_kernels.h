@@ -20,9 +20,6 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_FWD_BULK_STAGES
 #define SHINE_FWD_BULK_STAGES 6   // shared-memory slots of the forward's bulk staging ring
 #endif
-#ifndef SHINE_FWD_UNROLL
-#define SHINE_FWD_UNROLL 2        // forward steps per loop iteration with bulk staging
-#endif
 #ifndef SHINE_FWD_MIN_BLOCKS
 #define SHINE_FWD_MIN_BLOCKS 4    // resident CTAs per SM the forward register budget must allow
 #endif
@@ -44,7 +41,6 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 constexpr int kFwdThreads = 128;  // 4 warps per CTA
 constexpr int kFwdStages = SHINE_FWD_STAGES;
 constexpr int kFwdBulkStages = SHINE_FWD_BULK_STAGES;
-constexpr int kFwdUnroll = SHINE_FWD_UNROLL;
 constexpr int kBwdThreads = 128;
 constexpr int kBwdStages = SHINE_BWD_STAGES;
 
