@@ -18,7 +18,7 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #define SHINE_FWD_TMA 1           // forward interior segments staged by bulk copies
 #endif
 #ifndef SHINE_FWD_BULK_STAGES
-#define SHINE_FWD_BULK_STAGES 6   // shared-memory slots of the forward's bulk staging ring
+#define SHINE_FWD_BULK_STAGES 4   // shared-memory slots of the forward's bulk staging ring
 #endif
 #ifndef SHINE_FWD_MIN_BLOCKS
 #define SHINE_FWD_MIN_BLOCKS 4    // resident CTAs per SM the forward register budget must allow
