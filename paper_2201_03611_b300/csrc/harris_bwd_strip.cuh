@@ -186,20 +186,18 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
     // Register windows (row index relative to the lead image row r of the current step).
     float G0[6], G1[6], G2[6], G3[6], G4[6];  // gray rows r-4 .. r
     float2 I0[4], I1[4];                       // (Ix, Iy) rows r-3, r-2 (r-1 computed per step)
-    float2 gs0[4], gs1[4];                     // (gSxx, gSyy) rows r-4, r-3 (r-2 per step)
-    float gq0[4], gq1[4];                      // gSxy rows r-4, r-3
-    float2 gi0[6], gi1[6];                     // (gIx, gIy), zero outside the image, rows r-5, r-4
+    // Running sums (push form: each row is added into the sums it belongs to when it arrives):
+    float2 qa[4], qb[4];   // (gSxx, gSyy): rows k-1 and k summed, row k alone (k = r-3)
+    float qaq[4], qbq[4];  // gSxy likewise
+    float2 ga1[4], ga2[4]; // d gray of rows k-1 and k so far, x and y weight planes apart
     float gv[4];
 
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        gi0[i] = gi1[i] = make_float2(0.0f, 0.0f);
-        G0[i] = G1[i] = G2[i] = 0.0f;
-    }
+    for (int i = 0; i < 6; ++i) G0[i] = G1[i] = G2[i] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        I0[j] = I1[j] = gs0[j] = gs1[j] = make_float2(0.0f, 0.0f);
-        gq0[j] = gq1[j] = 0.0f;
+        I0[j] = I1[j] = qa[j] = qb[j] = ga1[j] = ga2[j] = make_float2(0.0f, 0.0f);
+        qaq[j] = qbq[j] = 0.0f;
     }
     stage_in(0, G3, gv);  // image rows r_first, r_first + 1; shifted down at every step
     stage_in(1, G4, gv);
@@ -292,7 +290,8 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
             dk[j] = -g * tr * tr;
         }
         if (own_row) partk += (dk[0] + dk[1]) + (dk[2] + dk[3]);
-        // B3: gP at row k = r-3 = clamped box sum of gS rows k-1, k, k+1.
+        // B3: gP at row k = r-3 = clamped box sum of gS rows k-1, k, k+1 (gS row k+1 arrives
+        // now): (k-1 + k) + k+1, with row k counted twice at either clamped image border.
         const int k = r - 3;
         float2 gp2[4];  // (gPxx, gPyy)
         float gpq[4];   // gPxy
@@ -303,15 +302,22 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 const bool top = k == 0, bot = k == H - 1;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    vg2[j] = __fadd2_rn(__fadd2_rn(top ? gs1[j] : gs0[j], gs1[j]), bot ? gs1[j] : gsn[j]);
-                    vgq[j] = ((top ? gq1[j] : gq0[j]) + gq1[j]) + (bot ? gq1[j] : gqn[j]);
+                    vg2[j] = __fadd2_rn(top ? __fadd2_rn(qb[j], qb[j]) : qa[j], bot ? qb[j] : gsn[j]);
+                    vgq[j] = (top ? qbq[j] + qbq[j] : qaq[j]) + (bot ? qbq[j] : gqn[j]);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    vg2[j] = __fadd2_rn(__fadd2_rn(gs0[j], gs1[j]), gsn[j]);
-                    vgq[j] = (gq0[j] + gq1[j]) + gqn[j];
+                    vg2[j] = __fadd2_rn(qa[j], gsn[j]);
+                    vgq[j] = qaq[j] + gqn[j];
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                qa[j] = __fadd2_rn(qb[j], gsn[j]);
+                qb[j] = gsn[j];
+                qaq[j] = qbq[j] + gqn[j];
+                qbq[j] = gqn[j];
             }
             horizontal_box<EDGE>(vg2, gp2, x, W);
             horizontal_box<EDGE>(vgq, gpq, x, W);
@@ -347,37 +353,33 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         float2 gin[6];
         make_row6(gI, gin);
 
-        // B5 (image) + B6 at row u = r-4: transposed stencil over gI rows u-1 (gi0), u (gi1),
-        // u+1 (gin), with the vertical clamp folds, then the horizontal folds, then store.
+        // B5 (image) + B6 at row u = r-4: the transposed stencil in push form. gI row k = u+1
+        // arrives: its taps complete d gray of row u and are added into rows k and k+1. The
+        // padded row -1 (complete when row 0 arrives) folds onto row 0, the padded row H
+        // (complete once row H-1 has arrived) onto row H-1.
         const int u = r - 4;
+        float2 done[4];
+        if (gimg != nullptr) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 d = ga1[j], n1 = ga2[j], n2 = make_float2(0.0f, 0.0f);
+                const float2 below = ga2[j];  // d gray of row u+1 so far
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int c = j - b + 2;  // gI column (lane column j) - b + 1 in row6 coordinates
+                    d = __ffma2_rn(P.w[b], gin[c], d);
+                    n1 = __ffma2_rn(P.w[3 + b], gin[c], n1);
+                    n2 = __ffma2_rn(P.w[6 + b], gin[c], n2);
+                }
+                if (!FAST && u == H - 1) d = __fadd2_rn(d, below);
+                if (!FAST && k == 0) n1 = __fadd2_rn(n1, d);
+                done[j] = d; ga1[j] = n1; ga2[j] = n2;
+            }
+        }
         if ((FAST || u >= y0) && gimg != nullptr) {
             float gg[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float2 t = make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const int c = j - b + 2;  // gI column v - b + 1 in row6 coordinates
-                    t = __ffma2_rn(P.w[b], gin[c], t);
-                    t = __ffma2_rn(P.w[3 + b], gi1[c], t);
-                    t = __ffma2_rn(P.w[6 + b], gi0[c], t);
-                }
-                gg[j] = t.x + t.y;
-            }
-            if (!FAST && (u == 0 || u == H - 1)) {
-                // padded row -1 (weights row 0) and row H (weights row 2) fold onto row u
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float2 t = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        const int c = j - b + 2;
-                        if (u == 0) t = __ffma2_rn(P.w[b], gi1[c], t);
-                        if (u == H - 1) t = __ffma2_rn(P.w[6 + b], gi1[c], t);
-                    }
-                    gg[j] += t.x + t.y;
-                }
-            }
+            for (int j = 0; j < 4; ++j) gg[j] = done[j].x + done[j].y;
             if constexpr (EDGE) {
                 // padded column -1 folds onto column 0, column W onto column W-1
                 float r6[6];
@@ -420,13 +422,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         }
         // shift the windows
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            I0[j] = I1[j]; I1[j] = I2[j];
-            gs0[j] = gs1[j]; gs1[j] = gsn[j];
-            gq0[j] = gq1[j]; gq1[j] = gqn[j];
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) { gi0[i] = gi1[i]; gi1[i] = gin[i]; }
+        for (int j = 0; j < 4; ++j) { I0[j] = I1[j]; I1[j] = I2[j]; }
     };
     auto flush = [&]() {
         acc[0] += partk;
