@@ -293,6 +293,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["fused_step"] = fused_extra(S, device, size, reps=max(10, K // 10))
         extras["precision"] = precision_extra(S, device, size, reps=max(10, K // 10))
         extras["batched"] = batched_extra(S, device, n=512, reps=20)
+        extras["mv"] = mv_extra(S, device, n=16384, reps=50)
         line["extras"] = extras
     return line
 
@@ -391,6 +392,30 @@ def fused_extra(S, device, size: int, reps: int) -> dict:
     return {"ms": t, "gpix_s": px / (t * 1e-3) / 1e9, "algorithmic_bytes_per_px": 32,
             "frac_of_measured_hbm": 32 * px / (t * 1e-3) / 1e9 / _peaks()[0],
             "equals_separate_passes": same}
+
+
+def mv_extra(S, device, n: int, reps: int) -> dict:
+    """The paper's running example, matrix-vector multiply, as an HBM-bound GEMV: an n x n
+    matrix (float32 and bf16 storage, larger than L2) times a float32 vector. Algorithmic
+    bytes: the matrix once, x and y once."""
+    A, x = wl.mv_inputs(n, n, seed=0)
+    xd = x.to(device)
+    y = torch.empty(n, device=device)
+    stream = torch.cuda.current_stream(device)
+    out = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        Ad = A.to(dt).to(device)
+        fn = lambda: S.mv(Ad, xd, out=y)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = _time_ms(fn, reps, stream)
+        nbytes = n * n * Ad.element_size() + 2 * n * 4
+        out[name] = {"ms": t, "gb_s": nbytes / (t * 1e-3) / 1e9, "frac_of_measured_hbm": nbytes / (t * 1e-3) / 1e9 / _peaks()[0],
+                     "algorithmic_bytes": nbytes}
+        del Ad
+    out["shape"] = [n, n]
+    return out
 
 
 def batched_extra(S, device, n: int, reps: int) -> dict:

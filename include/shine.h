@@ -224,6 +224,25 @@ SHINE_API void shine_plan_destroy(shine_plan* plan);
  */
 SHINE_API int shine_tune_key(char* buf, size_t len);
 
+/*
+ * Matrix-vector multiply, the paper's running example (Sec. 4, MV):
+ *   y[i] = reduce(+, 0)(map(*)(zip(A[i], x)))  =  sum_j A[i][j] * x[j]
+ *   A      [M][lda] elements of type dt, row-major, lda >= max(N, 1) (device)
+ *   x      [N] float32 (device), y [M] float32 (device, overwritten; N == 0 gives zeros)
+ *   stream a cudaStream_t
+ * A row's reduce is split across the 32 lanes of a warp: lane l sums, with float32 fused
+ * multiply-adds in order, the 16-byte chunks l, l+32, ... of the row into four accumulators
+ * (chunk c into accumulator (c / 32) mod 4; elements past the last whole chunk by the lane
+ * that owns them), adds them as (a0 + a1) + (a2 + a3), and the 32 lane sums are combined by a
+ * fixed butterfly; results do not depend on the launch and repeat bit for bit. Rows are read
+ * once from HBM (16-byte streaming loads when A, lda * sizeof(dt) and x allow; element loads
+ * otherwise, summed per lane in element order). Shapes: 0 <= M, N <= 2^31. Errors: invalid
+ * shapes or NULL pointers -> SHINE_ERR_INVALID_ARG; A not aligned to its element size or x,
+ * y not 4-byte aligned -> SHINE_ERR_ALIGNMENT.
+ */
+SHINE_API shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda, shine_dtype dt, const float* x,
+                                float* y, void* stream);
+
 /* Static description of a status code. */
 SHINE_API const char* shine_status_string(shine_status s);
 

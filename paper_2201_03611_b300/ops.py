@@ -179,6 +179,24 @@ def pipeline_host(img_h, g_h, kappa, wx, wy, dev_img, dev_g, dev_out, dev_gimg, 
                                         _stream(dev_img.device)), "shine_pipeline_host")
 
 
+def mv(A: torch.Tensor, x: torch.Tensor, out=None) -> torch.Tensor:
+    """y = A x (shine_mv): A is an (M, N) CUDA tensor (float32, bfloat16 or float16) with column
+    stride 1, x an (N,) float32 CUDA tensor; y is float32."""
+    if not A.is_cuda or A.dim() != 2 or (A.shape[1] > 1 and A.stride(1) != 1):
+        raise ValueError("A must be a 2-D CUDA tensor with column stride 1")
+    m, n = A.shape
+    if not x.is_cuda or x.dtype != torch.float32 or x.shape != (n,) or (n > 1 and x.stride(0) != 1):
+        raise ValueError(f"x must be a contiguous float32 CUDA tensor of shape ({n},)")
+    if out is None:
+        out = torch.empty(m, device=A.device, dtype=torch.float32)
+    if out.shape != (m,) or out.dtype != torch.float32 or (m > 1 and out.stride(0) != 1):
+        raise ValueError(f"out must be a contiguous float32 tensor of shape ({m},)")
+    lda = A.stride(0) if m > 1 else max(n, 1)
+    L.check(L.lib().shine_mv(_ptr(A), m, n, lda, dtype_code(A.dtype), _ptr(x), _ptr(out), _stream(A.device)),
+            "shine_mv")
+    return out
+
+
 def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
     if isinstance(v, torch.Tensor):
         return v

@@ -130,6 +130,25 @@ def test_mv_example_against_a_double_loop_and_numpy():
         MV.mv_opt(M.tolist(), x.tolist(), 5)     # split(5) of 12 rows is ill-typed
 
 
+def test_mv_rows_equals_the_pattern_form():
+    """The row-sampled MV (numpy dot as the row reduction) equals the list form of Sec. 4 to
+    FP64 rounding, on every row and on a chosen subset, and its scale is sum |a x|."""
+    rng = np.random.default_rng(11)
+    n, m = 9, 33
+    M = rng.standard_normal((n, m))
+    x = rng.standard_normal(m)
+    y = MV.mv(M.tolist(), x.tolist())
+    scale = np.abs(M) @ np.abs(x)
+    assert np.all(np.abs(MV.mv_rows(M, x) - y) <= 64 * 2.0 ** -53 * scale)
+    rows = [7, 0, 3]
+    assert np.array_equal(MV.mv_rows(M, x, rows), MV.mv_rows(M, x)[rows])
+    assert np.allclose(MV.mv_abs_rows(M, x, rows), scale[rows], rtol=1e-15, atol=0)
+    # closed forms: a row of ones against x sums x; a zero vector gives zeros
+    ones = np.ones((2, m))
+    assert np.allclose(MV.mv_rows(ones, x), [math.fsum(x)] * 2, rtol=0, atol=1e-14)
+    assert np.array_equal(MV.mv_rows(M, np.zeros(m)), np.zeros(n))
+
+
 def test_iterate_typing_and_value():
     """Sec. 6: iterate over Array[(n^k)*m] with a body that shrinks by n gives Array[m]."""
     n, k, m = 2, 3, 5

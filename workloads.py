@@ -136,3 +136,12 @@ def sample_points(h: int, w: int, n: int, seed: int, border_rows: int = 3) -> to
             edge.append((y, x))
     pts = torch.cat([torch.stack([ys, xs], 1), torch.tensor(edge, dtype=torch.int64).reshape(-1, 2)])
     return pts
+
+
+def mv_inputs(m: int, n: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
+    """Matrix-vector workload (the paper's running example): A ~ N(0,1) of shape (m, n), then
+    x ~ N(0,1) of shape (n,), float32, from one generator in that order."""
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn(m, n, generator=g)
+    x = torch.randn(n, generator=g)
+    return A, x
