@@ -294,6 +294,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["precision"] = precision_extra(S, device, size, reps=max(10, K // 10))
         extras["batched"] = batched_extra(S, device, n=512, reps=20)
         extras["mv"] = mv_extra(S, device, n=16384, reps=50)
+        extras["corners"] = corners_extra(S, device, size, reps=max(10, K // 10))
         line["extras"] = extras
     return line
 
@@ -392,6 +393,32 @@ def fused_extra(S, device, size: int, reps: int) -> dict:
     return {"ms": t, "gpix_s": px / (t * 1e-3) / 1e9, "algorithmic_bytes_per_px": 32,
             "frac_of_measured_hbm": 32 * px / (t * 1e-3) / 1e9 / _peaks()[0],
             "equals_separate_passes": same}
+
+
+def corners_extra(S, device, size: int, reps: int) -> dict:
+    """The corner step fused after the forward pass (threshold + 3x3 non-maximum suppression)
+    on the salt workload, float32: mask only (image 12 B in, mask 1 B out per pixel) and with
+    R written as well (+4 B)."""
+    img_h = wl.salt_image(size, size) if size != 8192 else wl.salt_8192()["img"]
+    img = img_h.to(device)
+    wx, wy = wl.sobel_weights()
+    k = torch.tensor([wl.KAPPA], device=device)
+    dwx, dwy = wx.to(device), wy.to(device)
+    mask = torch.empty(size, size, dtype=torch.uint8, device=device)
+    r = torch.empty(size, size, device=device)
+    stream = torch.cuda.current_stream(device)
+    px = size * size
+    out = {"threshold": wl.CORNER_THRESHOLD}
+    for name, o, bpp in (("mask", None, 13), ("mask_and_R", r, 17)):
+        fn = lambda: S.corners(img, k, dwx, dwy, wl.CORNER_THRESHOLD, "clamp", mask=mask, out=o)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = _time_ms(fn, reps, stream)
+        out[name] = {"ms": t, "gpix_s": px / (t * 1e-3) / 1e9, "algorithmic_bytes_per_px": bpp,
+                     "frac_of_measured_hbm": bpp * px / (t * 1e-3) / 1e9 / _peaks()[0]}
+    out["corners"] = int(mask.sum().item())
+    return out
 
 
 def mv_extra(S, device, n: int, reps: int) -> dict:

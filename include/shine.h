@@ -225,6 +225,24 @@ SHINE_API void shine_plan_destroy(shine_plan* plan);
 SHINE_API int shine_tune_key(char* buf, size_t len);
 
 /*
+ * Corner detection: the forward pass followed, in the same kernel, by a threshold and a 3x3
+ * non-maximum suppression of R (one more map over slide2D(3,1) windows, fused after A5):
+ *   mask[y][x] = 1  if R[y][x] > threshold and R[y][x] >= R at each of its 8 neighbours that
+ *                   lie inside the output region (neighbours outside it are ignored),
+ *                0  otherwise.
+ * R is the value shine_pipeline_fwd computes, bit for bit (same kernel arithmetic); ties keep
+ * every tied maximum. A NaN R is never a corner.
+ *   mask       [H_out][mask_pitch] bytes (uint8, device), mask_pitch >= W_out
+ *   out        optional R, as in shine_pipeline_fwd (NULL: R is not written; out_dt ignored)
+ *   threshold  host float32 value
+ * Other arguments, shapes and errors as in shine_pipeline_fwd; mask must not be NULL.
+ */
+SHINE_API shine_status shine_corners(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                                     shine_border border, const float* kappa, const float* wx, const float* wy,
+                                     float threshold, uint8_t* mask, int64_t mask_pitch, void* out,
+                                     int64_t out_pitch, shine_dtype out_dt, void* stream);
+
+/*
  * Matrix-vector multiply, the paper's running example (Sec. 4, MV):
  *   y[i] = reduce(+, 0)(map(*)(zip(A[i], x)))  =  sum_j A[i][j] * x[j]
  *   A      [M][lda] elements of type dt, row-major, lda >= max(N, 1) (device)

@@ -11,5 +11,6 @@ Python binding never do, and this package never imports them: the two share no c
 * ``cref``      -- the same pipeline as FP64 C loops, stage by stage (``harris_ref.c``), with
                    point-sampled forms for images too large for full FP64 stage arrays.
 * ``mv``        -- the paper's running example (matrix-vector multiply) in both its high-level
-                   and its optimised pattern form.
+                   and its optimised pattern form, and a row-sampled form for large matrices.
+* ``corners``   -- threshold + 3x3 non-maximum suppression of R (the corner step after A5).
 """

@@ -145,6 +145,38 @@ shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t i
     return cuda_status(launch_harris_fwd(a, dt, out_dt, static_cast<cudaStream_t>(stream)));
 }
 
+shine_status shine_corners(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                           shine_border border, const float* kappa, const float* wx, const float* wy, float threshold,
+                           uint8_t* mask, int64_t mask_pitch, void* out, int64_t out_pitch, shine_dtype out_dt,
+                           void* stream) {
+    if (!img || !kappa || !wx || !wy || !mask) return SHINE_ERR_INVALID_ARG;
+    if (!dtype_ok(dt) || (out && !dtype_ok(out_dt))) return SHINE_ERR_INVALID_ARG;
+    if (out && !(out_dt == dt || out_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
+    shine_status st = check_shape(H, W, border);
+    if (st != SHINE_OK) return st;
+    const int64_t Wo = border == SHINE_VALID ? W - 4 : W;
+    if (img_pitch < 3 * W || mask_pitch < Wo || (out && out_pitch < Wo)) return SHINE_ERR_INVALID_ARG;
+    const size_t si = dtype_size(dt), so = out ? dtype_size(out_dt) : si;
+    if (!aligned_to(img, si) || (out && !aligned_to(out, so)) || !aligned_to(kappa, 4) || !aligned_to(wx, 4) ||
+        !aligned_to(wy, 4))
+        return SHINE_ERR_ALIGNMENT;
+    CornerArgs c;
+    FwdArgs& a = c.f;
+    static_cast<Geometry&>(a) = fwd_geometry(H, W, border);
+    a.img = img; a.img_pitch = img_pitch; a.out = out; a.out_pitch = out ? out_pitch : 0;
+    a.kappa = kappa; a.wx = wx; a.wy = wy;
+    const size_t chunk = si == 4 ? 16 : 8;
+    a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
+    a.out_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
+    a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
+    a.err = nullptr;
+    c.mask = mask;
+    c.mask_pitch = mask_pitch;
+    c.threshold = threshold;
+    c.mask_vec = border == SHINE_CLAMP && aligned_to(mask, 4) && mask_pitch % 4 == 0;
+    return cuda_status(launch_harris_corners(c, dt, out ? out_dt : dt, static_cast<cudaStream_t>(stream)));
+}
+
 shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border border, size_t* bytes) {
     if (!bytes) return SHINE_ERR_INVALID_ARG;
     shine_status st = check_shape(H, W, border);

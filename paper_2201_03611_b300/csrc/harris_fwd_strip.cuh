@@ -93,9 +93,10 @@ __device__ __forceinline__ void fwd_strip_core(const Params& P, int x, int W, in
     }
 }
 
-// Strip with register staging (D rows in flight): every segment kind, any alignment.
-template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED>
-__device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
+// Rows y0 .. y1-1 of a strip with register staging (D rows in flight), for every segment kind
+// and alignment; store(y, R) receives each row's R at the lane's 4 columns.
+template <typename TI, int D, bool EDGE, bool ALIGNED, typename Store>
+__device__ __forceinline__ void fwd_rows(const FwdArgs& a, const Params& P, int x, int y0, int y1, Store&& store) {
     const int H = a.H, W = a.W;
     const RegRows<TI, EDGE, ALIGNED> rows(static_cast<const TI*>(a.img), a.img_pitch, x, W);
     const int r_first = y0 - 2;     // sequence row q is image row r_first + q (clamped)
@@ -109,32 +110,17 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
         if (q + D < nrows) rows.load(clampi(r_first + q + D, H), buf[k]);
         gray_row<EDGE>(v, g6, x, W);
     };
-    TO* out = static_cast<TO*>(a.out);
-    const bool producer = lane >= 1 && lane <= 30;
-    auto store = [&](int y, const float R[4]) {
-        if (!producer) return;
-        TO* orow = out + (int64_t)(y - a.oy) * a.out_pitch;
-        if (!EDGE && a.out_vec) {
-            store4(orow + x, R);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = x + j;
-                if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
-            }
-        }
-    };
     fwd_strip_core<EDGE, D>(P, x, W, H, y0, y1, take, store, [] { return true; });
 }
 
-// Strip of an interior segment with 16-byte aligned rows, staged by bulk (TMA) copies: lane 0
-// moves each row's whole 128-pixel segment into a ring of NS shared-memory slots with one copy
-// completing on the slot's mbarrier, so NS rows are in flight without holding registers. The
-// ring position and the row pointers are strength-reduced: per row the warp does the barrier
-// wait, three shared loads, one copy issue and the arithmetic.
-template <typename TI, typename TO, int NS>
-__device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
-                                               const TI* ring, FwdBulk& bulk) {
+// The same for an interior segment with 16-byte aligned rows, staged by bulk (TMA) copies:
+// lane 0 moves each row's whole 128-pixel segment into a ring of NS shared-memory slots with
+// one copy completing on the slot's mbarrier, so NS rows are in flight without holding
+// registers. The ring position and the row pointers are strength-reduced: per row the warp
+// does the barrier wait, three shared loads, one copy issue and the arithmetic.
+template <typename TI, int NS, typename Store>
+__device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                              const TI* ring, FwdBulk& bulk, Store&& store) {
     const int H = a.H;
     const int nrows = y1 - y0 + 4;  // gray rows y0-2 .. y1+1 (sequence rows 0 .. nrows-1)
     constexpr int kSlot = kLanes * 12;  // elements per slot
@@ -186,13 +172,6 @@ __device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P
         if (++slot == NS) { slot = 0; phase ^= 1u; }
         gray_row<false>(v, g6, x, 0);
     };
-    TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
-    const int64_t opitch = a.out_pitch;
-    const bool producer = lane >= 1 && lane <= 30;
-    auto store = [&](int, const float R[4]) {
-        if (producer) store4(orow, R);
-        orow += opitch;
-    };
     fwd_strip_core<false, 1>(P, x, 0, H, y0, y1, take, store, [&] { return !bulk.failed; });
     if (bulk.failed) {
         // Drain the copies issued but not seen complete (bounded waits), so that no bulk copy
@@ -203,6 +182,39 @@ __device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P
         }
     }
     bulk.seq = seq0 + (uint32_t)nrows;
+}
+
+// Forward strips that write R: any segment (register staging) ...
+template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED>
+__device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
+    TO* out = static_cast<TO*>(a.out);
+    const bool producer = lane >= 1 && lane <= 30;
+    fwd_rows<TI, D, EDGE, ALIGNED>(a, P, x, y0, y1, [&](int y, const float R[4]) {
+        if (!producer) return;
+        TO* orow = out + (int64_t)(y - a.oy) * a.out_pitch;
+        if (!EDGE && a.out_vec) {
+            store4(orow + x, R);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = x + j;
+                if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
+            }
+        }
+    });
+}
+
+// ... and interior segments staged by bulk copies (R stored with vector stores).
+template <typename TI, typename TO, int NS>
+__device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                               const TI* ring, FwdBulk& bulk) {
+    TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
+    const int64_t opitch = a.out_pitch;
+    const bool producer = lane >= 1 && lane <= 30;
+    fwd_rows_bulk<TI, NS>(a, P, lane, x, y0, y1, ring, bulk, [&](int, const float R[4]) {
+        if (producer) store4(orow, R);
+        orow += opitch;
+    });
 }
 
 }  // namespace shine

@@ -102,6 +102,16 @@ struct FwdArgs : Geometry {
     unsigned int* err;  // nonzero after a bounded wait gave up (nullable)
 };
 
+// Corner detection: the forward pass plus threshold and 3x3 non-maximum suppression of R.
+// f.out (R) may be null; the mask is one byte per output pixel.
+struct CornerArgs {
+    FwdArgs f;
+    uint8_t* mask;
+    int64_t mask_pitch;  // bytes
+    float threshold;
+    int mask_vec;        // mask rows can be written 4 bytes at a time
+};
+
 // The backward pass always covers every image pixel (its output is d img, H x W), so its
 // Geometry is the full image; the cotangent grad_out sits at (oy, ox) inside it with size
 // (gho, gwo) (VALID: offset 2 and size (H-4, W-4); CLAMP: offset 0 and size (H, W)).
@@ -133,6 +143,7 @@ struct BwdArgs : Geometry {
 // no more than leaves each warp min_rows rows. The backward's partials need
 // kParamSlots x a.nwarps doubles; *nwarps_used (nullable) reports the count.
 cudaError_t launch_harris_fwd(FwdArgs a, int dt, int out_dt, cudaStream_t s);
+cudaError_t launch_harris_corners(CornerArgs c, int dt, int out_dt, cudaStream_t s);
 cudaError_t launch_harris_bwd(BwdArgs a, int dt, int gout_dt, int max_warps, cudaStream_t s, int* nwarps_used);
 constexpr int kFwdMinRows = 16;  // minimum rows per warp slice
 constexpr int kBwdMinRows = 32;

@@ -98,6 +98,31 @@ def pipeline_fwd(img, kappa, wx, wy, border: str = "clamp", out_dtype=None, out=
     return out
 
 
+def corners(img, kappa, wx, wy, threshold: float, border: str = "clamp", mask=None, out=None, out_dtype=None):
+    """Corner mask (uint8, 1 where R > threshold and R >= its 8 neighbours inside the output) of
+    the fused forward + non-maximum suppression kernel (shine_corners). With out (or out_dtype)
+    the kernel also writes R; returns (mask, R or None)."""
+    _check_img(img)
+    _param(kappa, "kappa", 1); _param(wx, "wx", 9); _param(wy, "wy", 9)
+    h, w = img.shape[0], img.shape[1]
+    ho, wo = output_shape(h, w, border)
+    if mask is None:
+        mask = torch.empty(ho, wo, device=img.device, dtype=torch.uint8)
+    if mask.dtype != torch.uint8:
+        raise TypeError("mask must be uint8")
+    _check_map(mask, (ho, wo), "mask")
+    if out is None and out_dtype is not None:
+        out = torch.empty(ho, wo, device=img.device, dtype=out_dtype)
+    if out is not None:
+        _check_map(out, (ho, wo), "out")
+    L.check(L.lib().shine_corners(_ptr(img), h, w, _row_pitch(img), dtype_code(img.dtype), border_code(border),
+                                  _ptr(kappa), _ptr(wx), _ptr(wy), float(threshold), _ptr(mask), _row_pitch(mask),
+                                  _ptr(out), _row_pitch(out) if out is not None else 0,
+                                  dtype_code(out.dtype) if out is not None else dtype_code(img.dtype),
+                                  _stream(img.device)), "shine_corners")
+    return mask, out
+
+
 def _grads_out(img, need_img, need_params, grad_img=None):
     dev = img.device
     gimg = grad_img if grad_img is not None else (torch.empty_like(img) if need_img else None)

@@ -26,6 +26,9 @@ import math
 import torch
 
 KAPPA = 0.04
+# Corner threshold of the salt workloads: about the top 1% of R on the salted uniform image
+# (R quantiles there: 50% ~ 13, 90% ~ 41, 99% ~ 95); the corners are the local maxima above it.
+CORNER_THRESHOLD = 100.0
 
 # Default Sobel weights, applied as a correlation (window[a][b] * W[a][b]); x is the column.
 SOBEL_X = [[-1.0, 0.0, 1.0], [-2.0, 0.0, 2.0], [-1.0, 0.0, 1.0]]
