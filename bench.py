@@ -294,6 +294,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["precision"] = precision_extra(S, device, size, reps=max(10, K // 10))
         extras["batched"] = batched_extra(S, device, n=512, reps=20)
         extras["mv"] = mv_extra(S, device, n=16384, reps=50)
+        extras["iterate"] = iterate_extra(S, device, reps=50)
         extras["corners"] = corners_extra(S, device, size, reps=max(10, K // 10))
         line["extras"] = extras
     return line
@@ -419,6 +420,23 @@ def corners_extra(S, device, size: int, reps: int) -> dict:
                      "frac_of_measured_hbm": bpp * px / (t * 1e-3) / 1e9 / _peaks()[0]}
     out["corners"] = int(mask.sum().item())
     return out
+
+
+def iterate_extra(S, device, reps: int, m: int = 262144, n: int = 4, k: int = 5) -> dict:
+    """iterate with double buffering (Sec. 6): k rounds of split(n) >> map(reduce(+)) over
+    (n^k) m float32 values (1 GiB: larger than L2); the first round streams the input once,
+    the others run in shared memory. Algorithmic bytes: the input once and the output once."""
+    x = wl.iterate_inputs(m, n, k, seed=0).to(device)
+    y = torch.empty(m, device=device)
+    stream = torch.cuda.current_stream(device)
+    fn = lambda: S.iterate_sum(x, n, k, out=y)
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    t = _time_ms(fn, reps, stream)
+    nbytes = x.numel() * 4 + m * 4
+    return {"m": m, "n": n, "k": k, "ms": t, "gb_s": nbytes / (t * 1e-3) / 1e9,
+            "frac_of_measured_hbm": nbytes / (t * 1e-3) / 1e9 / _peaks()[0], "algorithmic_bytes": nbytes}
 
 
 def mv_extra(S, device, n: int, reps: int) -> dict:

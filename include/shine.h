@@ -243,6 +243,21 @@ SHINE_API shine_status shine_corners(const void* img, int64_t H, int64_t W, int6
                                      int64_t out_pitch, shine_dtype out_dt, void* stream);
 
 /*
+ * iterate with double buffering (Sec. 6): k rounds of the body split(n) >> map(reduce(+, 0))
+ * applied to Array[(n^k) * m], so that
+ *   out[j] = the level-by-level tree sum of in[j * n^k .. (j+1) * n^k): every round replaces
+ *            each n consecutive values by their left fold from 0 (((0 + a0) + a1) + ...).
+ *   in   [(n^k) * m] float32 (device), out [m] float32 (device, overwritten)
+ * The rounds ping-pong between two shared-memory buffers: round 0 reads the input straight
+ * from global memory, the last round writes out; every sum keeps the fold order above, so the
+ * result equals a float32 evaluation of the definition bit for bit. k == 0 copies m values.
+ * Limits: n >= 1, k >= 0, (n^k) * m <= 2^40; one group's n^(k-1) round-1 values must fit one
+ * buffer (6144 floats) when k > 1, else SHINE_ERR_UNSUPPORTED. Errors: bad sizes or NULL
+ * pointers -> SHINE_ERR_INVALID_ARG; in/out not 4-byte aligned -> SHINE_ERR_ALIGNMENT.
+ */
+SHINE_API shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, int32_t k, float* out, void* stream);
+
+/*
  * Matrix-vector multiply, the paper's running example (Sec. 4, MV):
  *   y[i] = reduce(+, 0)(map(*)(zip(A[i], x)))  =  sum_j A[i][j] * x[j]
  *   A      [M][lda] elements of type dt, row-major, lda >= max(N, 1) (device)

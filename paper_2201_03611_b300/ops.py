@@ -222,6 +222,23 @@ def mv(A: torch.Tensor, x: torch.Tensor, out=None) -> torch.Tensor:
     return out
 
 
+def iterate_sum(x: torch.Tensor, n: int, k: int, out=None) -> torch.Tensor:
+    """iterate(k, split(n) >> map(reduce(+, 0))) of a contiguous float32 CUDA vector of length
+    (n^k) m (shine_iterate_sum); returns the m tree sums."""
+    if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 1 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous 1-D float32 CUDA tensor")
+    span = n ** k
+    if n < 1 or k < 0 or x.numel() % span:
+        raise ValueError(f"length {x.numel()} is not a multiple of n^k = {span}")
+    m = x.numel() // span
+    if out is None:
+        out = torch.empty(m, device=x.device, dtype=torch.float32)
+    if out.shape != (m,) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous float32 tensor of shape ({m},)")
+    L.check(L.lib().shine_iterate_sum(_ptr(x), m, n, k, _ptr(out), _stream(x.device)), "shine_iterate_sum")
+    return out
+
+
 def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
     if isinstance(v, torch.Tensor):
         return v

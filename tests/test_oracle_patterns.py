@@ -177,3 +177,24 @@ def test_adjoints_satisfy_the_dot_product_identity():
     assert abs(_dot(P.slide2D(3, 1, x2), y2) - _dot(x2, P.slide2D_vjp(3, 1, h, w, y2))) < 1e-12
     y3 = rng.standard_normal((h + 2, w + 2)).tolist()
     assert abs(_dot(P.pad_clamp2D(1, 1, x2), y3) - _dot(x2, P.pad_clamp2D_vjp(1, 1, h, w, y3))) < 1e-12
+
+
+def test_iterate_sum_forms_agree_and_fix_the_tree():
+    """Sec. 6 with the summing body: the numpy rounds equal the pattern composition bit for
+    bit in float64 (same additions in the same order), every output is its group's tree sum,
+    and all-ones inputs give n^k exactly."""
+    from oracle import iterate_sum as IT
+    rng = np.random.default_rng(4)
+    for n, k, m in ((2, 3, 5), (3, 2, 4), (4, 3, 2), (5, 1, 7), (2, 0, 3)):
+        x = rng.standard_normal(n ** k * m)
+        a = IT.iterate_sum(x.tolist(), n, k)
+        b = IT.iterate_sum_np(x, n, k)
+        assert len(a) == m and np.array_equal(np.array(a), b)
+        exact = [math.fsum(x[j * n ** k:(j + 1) * n ** k]) for j in range(m)]
+        assert np.all(np.abs(b - exact) <= IT.tree_bound(x, n, k, 2.0 ** -53) + 1e-300)
+        assert np.array_equal(IT.iterate_sum_np(np.ones(n ** k * m), n, k), np.full(m, float(n ** k)))
+    # float32 rounds: the fold order matters, and the numpy form keeps the pattern's order
+    x32 = np.array([1.0, 2.0 ** -24, 2.0 ** -24, 2.0 ** -24], dtype=np.float32)
+    left = IT.iterate_sum_np(x32, 4, 1, np.float32)[0]
+    assert left == np.float32(1.0)                       # ((1 + e) + e) + e rounds back to 1
+    assert IT.iterate_sum_np(x32, 2, 2, np.float32)[0] == np.float32(1.0) + np.float32(2.0 ** -23)

@@ -148,3 +148,9 @@ def mv_inputs(m: int, n: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
     A = torch.randn(m, n, generator=g)
     x = torch.randn(n, generator=g)
     return A, x
+
+
+def iterate_inputs(m: int, n: int, k: int, seed: int) -> torch.Tensor:
+    """Input of the iterate (tree-sum) workload: (n^k) m float32 values ~ U(-1, 1)."""
+    g = torch.Generator().manual_seed(seed)
+    return torch.rand(n ** k * m, generator=g) * 2.0 - 1.0
