@@ -295,6 +295,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["batched"] = batched_extra(S, device, n=512, reps=20)
         extras["mv"] = mv_extra(S, device, n=16384, reps=50)
         extras["iterate"] = iterate_extra(S, device, reps=50)
+        extras["stencil"] = stencil_extra(S, device, size, reps=max(10, K // 20))
         extras["corners"] = corners_extra(S, device, size, reps=max(10, K // 10))
         line["extras"] = extras
     return line
@@ -437,6 +438,52 @@ def iterate_extra(S, device, reps: int, m: int = 262144, n: int = 4, k: int = 5)
     nbytes = x.numel() * 4 + m * 4
     return {"m": m, "n": n, "k": k, "ms": t, "gb_s": nbytes / (t * 1e-3) / 1e9,
             "frac_of_measured_hbm": nbytes / (t * 1e-3) / 1e9 / _peaks()[0], "algorithmic_bytes": nbytes}
+
+
+def stencil_extra(S, device, size: int, reps: int) -> dict:
+    """The generalised slide2D(K) + reduce stage on a size x size float32 array (8 B/px of HBM
+    traffic): K x K weights for K = 3, 5, 9 and the separable K = 9 form. Reports the FP32
+    FMA rate against the FP32 peak (SMs x 128 lanes x 2 flops x max SM clock) as well, since
+    the larger K are arithmetic-bound."""
+    out = {}
+    props = torch.cuda.get_device_properties(device)
+    clock_ghz = _max_sm_clock_ghz()
+    fp32_peak = props.multi_processor_count * 128 * 2 * clock_ghz / 1e3   # TFLOP/s
+    px = size * size
+    y = torch.empty(size, size, device=device)
+    stream = torch.cuda.current_stream(device)
+    for K, sep in ((3, False), (5, False), (9, False), (9, True)):
+        x, W = wl.stencil_inputs(size, size, K, seed=0)
+        xd = x.to(device)
+        if sep:
+            wv, wh = wl.separable_weights(K, seed=0)
+            fn = lambda: S.stencil2d(xd, wv=wv, wh=wh, out=y)
+            flops = 4 * K
+        else:
+            fn = lambda: S.stencil2d(xd, W, out=y)
+            flops = 2 * K * K
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = _time_ms(fn, reps, stream)
+        tf = flops * px / (t * 1e-3) / 1e12
+        out[f"K{K}{'_sep' if sep else ''}"] = {
+            "ms": t, "gpix_s": px / (t * 1e-3) / 1e9, "frac_of_measured_hbm": 8 * px / (t * 1e-3) / 1e9 / _peaks()[0],
+            "tflop_s": tf, "frac_of_fp32_peak": tf / fp32_peak}
+        del xd
+    out["fp32_peak_tflop_s"] = fp32_peak
+    out["fp32_peak_note"] = "derived: SMs x 128 FP32 lanes x 2 x max SM clock"
+    return out
+
+
+def _max_sm_clock_ghz() -> float:
+    try:
+        import subprocess
+        v = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                           capture_output=True, text=True, timeout=10).stdout.split()[0]
+        return float(v) / 1e3
+    except Exception:
+        return 2.032
 
 
 def mv_extra(S, device, n: int, reps: int) -> dict:

@@ -243,6 +243,30 @@ SHINE_API shine_status shine_corners(const void* img, int64_t H, int64_t W, int6
                                      int64_t out_pitch, shine_dtype out_dt, void* stream);
 
 /*
+ * Generalised stencil: one fused slide2D(K, 1) + reduce stage over a single-channel array,
+ *   out = map(map(nbh => reduce(+, 0)(map(*)(zip(join nbh, join W)))))(slide2D(K, 1)(pad(in)))
+ * K odd, 1 <= K <= 9, r = (K-1)/2; SHINE_CLAMP pads with pad_clamp2D(r) (output H x W),
+ * SHINE_VALID does not pad (output (H-2r) x (W-2r), needs H, W >= K). The weights act as a
+ * correlation: out[i][j] = sum_{a,b} W[a][b] * in_padded[i+a][j+b].
+ *   weights  HOST pointer to K*K float32, row-major (W[a][b] = weights[a*K + b]); or NULL for
+ *            the separable form, which then takes
+ *   wv, wh   HOST pointers to K float32 each: a K-tap stage down the columns with wv, then a
+ *            K-tap stage along the rows with wh (the composition of two 1-D slide + reduce
+ *            stages; equal to W = wv wh^T up to rounding).
+ * The weights are copied at the call into the kernel's parameters (they are not read later).
+ *   in   [H][in_pitch] elements of dt (device), out [H_out][out_pitch] of out_dt (device)
+ *   dt/out_dt: F32 -> F32, BF16 -> BF16 or F32 (float32 arithmetic throughout).
+ * Each output is a float32 fused multiply-add chain over its taps in row-major order from zero
+ * (separable: the column chain, then the row chain). Errors: bad K, shapes, pitches or NULL
+ * pointers -> SHINE_ERR_INVALID_ARG; other dtype pairs -> SHINE_ERR_UNSUPPORTED; misaligned
+ * elements -> SHINE_ERR_ALIGNMENT.
+ */
+SHINE_API shine_status shine_stencil2d(const void* in, int64_t H, int64_t W, int64_t in_pitch, shine_dtype dt,
+                                       shine_border border, int32_t K, const float* weights, const float* wv,
+                                       const float* wh, void* out, int64_t out_pitch, shine_dtype out_dt,
+                                       void* stream);
+
+/*
  * iterate with double buffering (Sec. 6): k rounds of the body split(n) >> map(reduce(+, 0))
  * applied to Array[(n^k) * m], so that
  *   out[j] = the level-by-level tree sum of in[j * n^k .. (j+1) * n^k): every round replaces

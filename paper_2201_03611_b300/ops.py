@@ -239,6 +239,43 @@ def iterate_sum(x: torch.Tensor, n: int, k: int, out=None) -> torch.Tensor:
     return out
 
 
+def stencil2d(x: torch.Tensor, weights=None, wv=None, wh=None, border: str = "clamp", out=None,
+              out_dtype=None) -> torch.Tensor:
+    """One slide2D(K, 1) + reduce stage (shine_stencil2d) of an (H, W) CUDA array (float32 or
+    bfloat16, column stride 1). weights: (K, K) host weights, or wv and wh (K each) for the
+    separable form. Weights are host values (CPU tensors or sequences)."""
+    if not x.is_cuda or x.dim() != 2 or (x.shape[1] > 1 and x.stride(1) != 1):
+        raise ValueError("x must be a 2-D CUDA tensor with column stride 1")
+    h, w = x.shape
+    if weights is not None:
+        wt = torch.as_tensor(weights, dtype=torch.float32).cpu().contiguous()
+        if wt.dim() != 2 or wt.shape[0] != wt.shape[1]:
+            raise ValueError("weights must be K x K")
+        K = wt.shape[0]
+        wp, vp, hp = ctypes.cast(wt.data_ptr(), ctypes.c_void_p), None, None
+        keep = (wt,)
+    else:
+        v = torch.as_tensor(wv, dtype=torch.float32).cpu().contiguous()
+        hh = torch.as_tensor(wh, dtype=torch.float32).cpu().contiguous()
+        if v.dim() != 1 or v.shape != hh.shape:
+            raise ValueError("wv and wh must be 1-D of the same length K")
+        K = v.shape[0]
+        wp, vp, hp = None, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(hh.data_ptr())
+        keep = (v, hh)
+    r = (K - 1) // 2
+    ho, wo = (h, w) if border == "clamp" else (h - 2 * r, w - 2 * r)
+    odt = x.dtype if out_dtype is None else out_dtype
+    if out is None:
+        out = torch.empty(max(ho, 0), max(wo, 0), device=x.device, dtype=odt)
+    _check_map(out, (ho, wo), "out")
+    L.check(L.lib().shine_stencil2d(_ptr(x), h, w, _row_pitch(x) if h > 1 else max(w, 1), dtype_code(x.dtype),
+                                    border_code(border), K, wp, vp, hp, _ptr(out),
+                                    _row_pitch(out) if out.shape[0] > 1 else max(wo, 1), dtype_code(out.dtype),
+                                    _stream(x.device)), "shine_stencil2d")
+    del keep
+    return out
+
+
 def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
     if isinstance(v, torch.Tensor):
         return v

@@ -154,3 +154,24 @@ def iterate_inputs(m: int, n: int, k: int, seed: int) -> torch.Tensor:
     """Input of the iterate (tree-sum) workload: (n^k) m float32 values ~ U(-1, 1)."""
     g = torch.Generator().manual_seed(seed)
     return torch.rand(n ** k * m, generator=g) * 2.0 - 1.0
+
+
+def stencil_inputs(h: int, w: int, k: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
+    """Generalised-stencil workload: x ~ U(0, 1) of shape (h, w), then K x K weights ~ N(0, 1)
+    (non-separable), float32, from one generator in that order."""
+    g = torch.Generator().manual_seed(seed)
+    x = torch.rand(h, w, generator=g)
+    W = torch.randn(k, k, generator=g)
+    return x, W
+
+
+def separable_weights(k: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
+    """A K-tap Gaussian down the columns (sigma = K / 4) and K ~ N(0, 1) taps along the rows."""
+    g = torch.Generator().manual_seed(seed + 7919)
+    r = (k - 1) // 2
+    t = torch.arange(-r, r + 1, dtype=torch.float64)
+    sigma = max(k / 4.0, 0.5)
+    wv = torch.exp(-0.5 * (t / sigma) ** 2)
+    wv = (wv / wv.sum()).float()
+    wh = torch.randn(k, generator=g)
+    return wv, wh
