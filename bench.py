@@ -296,6 +296,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["mv"] = mv_extra(S, device, n=16384, reps=50)
         extras["iterate"] = iterate_extra(S, device, reps=50)
         extras["stencil"] = stencil_extra(S, device, size, reps=max(10, K // 20))
+        extras["gaussian_window_harris"] = window_extra(S, device, size, reps=max(10, K // 20))
         extras["corners"] = corners_extra(S, device, size, reps=max(10, K // 10))
         line["extras"] = extras
     return line
@@ -484,6 +485,30 @@ def _max_sm_clock_ghz() -> float:
         return float(v) / 1e3
     except Exception:
         return 2.032
+
+
+def window_extra(S, device, size: int, reps: int) -> dict:
+    """Harris with a Gaussian window (K = 5 and 7 taps) at A4 instead of the 3x3 box, on the salt
+    workload, float32 (image 12 B in, R 4 B out per pixel)."""
+    img_h = wl.salt_image(size, size) if size != 8192 else wl.salt_8192()["img"]
+    img = img_h.to(device)
+    wx, wy = wl.sobel_weights()
+    k = torch.tensor([wl.KAPPA], device=device)
+    dwx, dwy = wx.to(device), wy.to(device)
+    o = torch.empty(size, size, device=device)
+    stream = torch.cuda.current_stream(device)
+    px = size * size
+    out = {}
+    for K in (5, 7):
+        gv, gh = wl.gaussian_window(K)
+        fn = lambda: S.harris_window(img, k, dwx, dwy, gv, gh, out=o)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = _time_ms(fn, reps, stream)
+        out[f"K{K}"] = {"ms": t, "gpix_s": px / (t * 1e-3) / 1e9,
+                        "frac_of_measured_hbm": 16 * px / (t * 1e-3) / 1e9 / _peaks()[0]}
+    return out
 
 
 def mv_extra(S, device, n: int, reps: int) -> dict:

@@ -243,6 +243,23 @@ SHINE_API shine_status shine_corners(const void* img, int64_t H, int64_t W, int6
                                      int64_t out_pitch, shine_dtype out_dt, void* stream);
 
 /*
+ * Harris with a weighted window: the forward pipeline with its A4 box replaced by a separable
+ * K-tap window (K = 3, 5, 7; e.g. Gaussian taps), fused into one kernel like the forward:
+ *   A1 gray, A2 3x3 Sobel (Wx, Wy, per-stage clamp), A3 products,
+ *   A4' S_c = sum_{a,b} gv[a] gh[b] P_c[clamp(i-r+a)][clamp(j-r+b)]   (r = (K-1)/2; computed as
+ *       the column sum with gv, then the row sum with gh, each a float32 fma chain from zero),
+ *   A5 R = Sxx Syy - Sxy^2 - kappa (Sxx + Syy)^2.
+ * CLAMP borders only (output H x W). gv, gh: HOST pointers to K float32 each (copied at the
+ * call). dt/out_dt: F32 -> F32, BF16 -> BF16 or F32. Other arguments as shine_pipeline_fwd.
+ * Errors: K not in {3, 5, 7}, bad shapes or NULL pointers -> SHINE_ERR_INVALID_ARG; other dtype
+ * pairs -> SHINE_ERR_UNSUPPORTED; misaligned pointers -> SHINE_ERR_ALIGNMENT.
+ */
+SHINE_API shine_status shine_harris_window(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                                           const float* kappa, const float* wx, const float* wy, int32_t K,
+                                           const float* gv, const float* gh, void* out, int64_t out_pitch,
+                                           shine_dtype out_dt, void* stream);
+
+/*
  * Generalised stencil: one fused slide2D(K, 1) + reduce stage over a single-channel array,
  *   out = map(map(nbh => reduce(+, 0)(map(*)(zip(join nbh, join W)))))(slide2D(K, 1)(pad(in)))
  * K odd, 1 <= K <= 9, r = (K-1)/2; SHINE_CLAMP pads with pad_clamp2D(r) (output H x W),

@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         "shine_mv": (st, [p, i64, i64, i64, f, p, p, p]),
         "shine_iterate_sum": (st, [p, i64, i32, i32, p, p]),
         "shine_stencil2d": (st, [p, i64, i64, i64, f, f, i32, p, p, p, p, i64, f, p]),
+        "shine_harris_window": (st, [p, i64, i64, i64, f, p, p, p, i32, p, p, p, i64, f, p]),
         "shine_corners": (st, [p, i64, i64, i64, f, f, p, p, p, ctypes.c_float, p, i64, p, i64, f, p]),
         "shine_plan_create": (st, [ctypes.POINTER(i64), i32, f, f, i32, ctypes.c_char_p, ctypes.POINTER(p)]),
         "shine_plan_workspace": (st, [p, ctypes.POINTER(sz)]),

@@ -317,6 +317,38 @@ __device__ __forceinline__ void make_row6(const float2 c[4], float2 r6[6]) {
     r6[5].y = __shfl_down_sync(kFull, c[0].y, 1);
 }
 
+// The lane's 4 values widened by R columns on each side from the neighbouring lanes (R <= 4).
+template <int R>
+__device__ __forceinline__ void widen(const float c[4], float e[4 + 2 * R]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e[R + j] = c[j];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        e[i] = __shfl_up_sync(kFull, c[4 - R + i], 1);
+        e[R + 4 + i] = __shfl_down_sync(kFull, c[i], 1);
+    }
+}
+
+// pad_clamp at this stage for a widened row of N values at columns xs .. xs+N-1: values at
+// columns outside [0, W) become the value at column 0 or W-1 (those columns are in the row
+// whenever a position needs them, except on lanes wholly outside the image, whose values are
+// never stored).
+template <int N>
+__device__ __forceinline__ void clamp_widened(float e[N], int xs, int W) {
+    const int i0 = -xs, iw = W - 1 - xs;
+    float v0 = e[0], vw = e[N - 1];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i == i0) v0 = e[i];
+        if (i == iw) vw = e[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (xs + i < 0) e[i] = v0;
+        else if (xs + i >= W) e[i] = vw;
+    }
+}
+
 // pad_clamp at this stage: the value at column -1 becomes the value at column 0 and the
 // value at column W becomes the value at column W-1. Only the stencil reads of in-image
 // columns matter, and those read at most one column beyond the edge.

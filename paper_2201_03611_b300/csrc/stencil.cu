@@ -66,18 +66,6 @@ __device__ __forceinline__ void load4(const StencilArgs& a, int x, int y, float 
     }
 }
 
-// The lane's 4 values widened by R on each side from the neighbouring lanes.
-template <int R>
-__device__ __forceinline__ void widen(const float c[4], float e[4 + 2 * R]) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) e[R + j] = c[j];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        e[i] = __shfl_up_sync(kFull, c[4 - R + i], 1);
-        e[R + 4 + i] = __shfl_down_sync(kFull, c[i], 1);
-    }
-}
-
 template <int K, bool SEP, typename TI, typename TO, bool EDGE, bool ALIGNED>
 __device__ __forceinline__ void stencil_strip(const StencilArgs& a, int lane, int x, int y0, int y1) {
     constexpr int R = (K - 1) / 2;

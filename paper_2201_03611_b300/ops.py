@@ -276,6 +276,26 @@ def stencil2d(x: torch.Tensor, weights=None, wv=None, wh=None, border: str = "cl
     return out
 
 
+def harris_window(img, kappa, wx, wy, gv, gh, out=None, out_dtype=None) -> torch.Tensor:
+    """R of the Harris pipeline with a separable K-tap window (gv down the columns, gh along the
+    rows; host values) at A4, CLAMP borders (shine_harris_window)."""
+    _check_img(img)
+    _param(kappa, "kappa", 1); _param(wx, "wx", 9); _param(wy, "wy", 9)
+    v = torch.as_tensor(gv, dtype=torch.float32).cpu().contiguous()
+    hh = torch.as_tensor(gh, dtype=torch.float32).cpu().contiguous()
+    if v.dim() != 1 or v.shape != hh.shape:
+        raise ValueError("gv and gh must be 1-D of the same length K")
+    h, w = img.shape[0], img.shape[1]
+    if out is None:
+        out = torch.empty(h, w, device=img.device, dtype=img.dtype if out_dtype is None else out_dtype)
+    _check_map(out, (h, w), "out")
+    L.check(L.lib().shine_harris_window(_ptr(img), h, w, _row_pitch(img), dtype_code(img.dtype), _ptr(kappa),
+                                        _ptr(wx), _ptr(wy), v.shape[0], ctypes.c_void_p(v.data_ptr()),
+                                        ctypes.c_void_p(hh.data_ptr()), _ptr(out), _row_pitch(out),
+                                        dtype_code(out.dtype), _stream(img.device)), "shine_harris_window")
+    return out
+
+
 def _as_param(v, like: torch.Tensor, shape) -> torch.Tensor:
     if isinstance(v, torch.Tensor):
         return v

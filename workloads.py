@@ -175,3 +175,13 @@ def separable_weights(k: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
     wv = (wv / wv.sum()).float()
     wh = torch.randn(k, generator=g)
     return wv, wh
+
+
+def gaussian_window(k: int, sigma: float | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Normalised K-tap Gaussian taps (sigma = K / 4 unless given) for both window axes."""
+    r = (k - 1) // 2
+    s = sigma if sigma is not None else max(k / 4.0, 0.5)
+    t = torch.arange(-r, r + 1, dtype=torch.float64)
+    w = torch.exp(-0.5 * (t / s) ** 2)
+    w = (w / w.sum()).float()
+    return w.clone(), w.clone()
