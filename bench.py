@@ -615,6 +615,18 @@ def run_reference(args, world, rank) -> dict | None:
             "e2e": {"value": value, "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# Extra workloads runnable alone (python bench.py --extra NAME --size N --steps K): the size is
+# the image side (or, for MV, the matrix side; for iterate, the total input is size^2 floats).
+EXTRAS = {
+    "fused_step": lambda S, d, n, r: fused_extra(S, d, n, r),
+    "corners": lambda S, d, n, r: corners_extra(S, d, n, r),
+    "mv": lambda S, d, n, r: mv_extra(S, d, n, r),
+    "iterate": lambda S, d, n, r: iterate_extra(S, d, r, m=n * n // 1024, n=4, k=5),
+    "stencil": lambda S, d, n, r: stencil_extra(S, d, n, r),
+    "gaussian_window_harris": lambda S, d, n, r: window_extra(S, d, n, r),
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -628,7 +640,16 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extra", choices=sorted(EXTRAS),
+                    help="run only this extra workload at --size (for profiling) and print its JSON")
     args = ap.parse_args()
+    if args.extra:
+        import paper_2201_03611_b300 as S
+        torch.cuda.set_device(0)
+        print(json.dumps({"extra": args.extra, "size": args.size,
+                          "result": EXTRAS[args.extra](S, torch.device("cuda", 0), args.size, max(3, args.steps))}),
+              flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = _dist()
