@@ -113,30 +113,40 @@ __device__ __forceinline__ void fwd_rows(const FwdArgs& a, const Params& P, int 
     fwd_strip_core<EDGE, D>(P, x, W, H, y0, y1, take, store, [] { return true; });
 }
 
-// The same for an interior segment with 16-byte aligned rows, staged by bulk (TMA) copies:
-// lane 0 moves each row's whole 128-pixel segment into a ring of NS shared-memory slots with
-// one copy completing on the slot's mbarrier, so NS rows are in flight without holding
-// registers. The ring position and the row pointers are strength-reduced: per row the warp
-// does the barrier wait, three shared loads, one copy issue and the arithmetic.
-template <typename TI, int NS, typename Store>
-__device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
-                                              const TI* ring, FwdBulk& bulk, Store&& store) {
-    const int H = a.H;
-    const int nrows = y1 - y0 + 4;  // gray rows y0-2 .. y1+1 (sequence rows 0 .. nrows-1)
-    constexpr int kSlot = kLanes * 12;  // elements per slot
-    constexpr uint32_t kBytes = kSegLoad * 3 * sizeof(TI);
-    const TI* seg = static_cast<const TI*>(a.img) + (int64_t)(x - 4 * lane) * 3;
-    const uint32_t ring0 = smem_u32(ring - lane * 12);  // slot 0 of the warp's ring
-    const uint32_t lane_ring = smem_u32(ring);          // this lane's 12 elements of slot 0
-    const uint32_t seq0 = bulk.seq;
-    uint32_t slot = seq0 % NS, phase = (seq0 / NS) & 1u;  // next row to take
-    int fq = 0;  // next sequence row to fetch; it goes to the slot of row fq - NS
-    uint32_t fslot = slot;
-    int tq = 0, failed_q = 0;  // rows taken; the first row whose wait gave up
+// Bulk (TMA) staging of a warp's stream of gray rows g_first .. g_first+n-1 of an interior
+// segment with 16-byte aligned rows: lane 0 moves each row's whole 128-pixel segment into a
+// ring of NS shared-memory slots with one copy completing on the slot's mbarrier, so NS rows are
+// in flight without holding registers. The ring position and the row pointers are
+// strength-reduced: per row the warp does the barrier wait, three shared loads, one copy issue
+// and the gray arithmetic. finish() must follow the last take().
+template <typename TI, int NS>
+struct BulkGray {
+    static constexpr int kSlot = kLanes * 12;  // elements per slot
+    static constexpr uint32_t kBytes = kSegLoad * 3 * sizeof(TI);
+    const FwdArgs& a;
+    FwdBulk& bulk;
+    const int lane, x, g_first, n;
+    const TI* seg;
+    uint32_t ring0, lane_ring, seq0, slot, phase, fslot;
+    int fq = 0, tq = 0, failed_q = 0;  // next row to fetch; rows taken; first row whose wait gave up
 
-    auto fetch = [&]() {
+    __device__ __forceinline__ BulkGray(const FwdArgs& a_, FwdBulk& bulk_, const TI* ring, int lane_, int x_,
+                                        int g_first_, int n_)
+        : a(a_), bulk(bulk_), lane(lane_), x(x_), g_first(g_first_), n(n_) {
+        seg = static_cast<const TI*>(a.img) + (int64_t)(x - 4 * lane) * 3;
+        ring0 = smem_u32(ring - lane * 12);  // slot 0 of the warp's ring
+        lane_ring = smem_u32(ring);          // this lane's 12 elements of slot 0
+        seq0 = bulk.seq;
+        slot = seq0 % NS;
+        phase = (seq0 / NS) & 1u;
+        fslot = slot;
+#pragma unroll 1
+        for (int i = 0; i < NS && fq < n; ++i) fetch();
+    }
+    // Row fq goes to the slot of row fq - NS.
+    __device__ __forceinline__ void fetch() {
         if (lane == 0) {
-            const TI* src = seg + (int64_t)clampi(y0 - 2 + fq, H) * a.img_pitch;
+            const TI* src = seg + (int64_t)clampi(g_first + fq, a.H) * a.img_pitch;
             const uint32_t bar = bulk.bars + 8 * fslot;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, kBytes);
@@ -144,12 +154,9 @@ __device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P,
         }
         ++fq;
         fslot = fslot + 1 == NS ? 0 : fslot + 1;
-    };
-#pragma unroll 1
-    for (int i = 0; i < NS && fq < nrows; ++i) fetch();
-
-    // Take the next row as a gray row; its slot is then refilled with the row NS further on.
-    auto take = [&](int, int, float g6[6]) {
+    }
+    // The next row as a gray row; its slot is then refilled with the row NS further on.
+    __device__ __forceinline__ void take(float g6[6]) {
         const bool ok = warp_mbar_wait(bulk.bars + 8 * slot, phase, lane);
         if (!ok && !bulk.failed) { bulk.failed = true; failed_q = tq; }
         ++tq;
@@ -168,20 +175,31 @@ __device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P,
             RegRows<TI, false, true>::unpack(r, v);
         }
         __syncwarp();  // every lane has read the slot before the copy that overwrites it
-        if (!bulk.failed && fq < nrows) fetch();
+        if (!bulk.failed && fq < n) fetch();
         if (++slot == NS) { slot = 0; phase ^= 1u; }
         gray_row<false>(v, g6, x, 0);
-    };
-    fwd_strip_core<false, 1>(P, x, 0, H, y0, y1, take, store, [&] { return !bulk.failed; });
-    if (bulk.failed) {
-        // Drain the copies issued but not seen complete (bounded waits), so that no bulk copy
-        // still writes this warp's shared memory when the kernel returns.
-        for (int q = failed_q; q < fq; ++q) {
-            const uint32_t n = seq0 + (uint32_t)q;
-            mbar_wait(bulk.bars + 8 * (n % NS), (n / NS) & 1u);
-        }
     }
-    bulk.seq = seq0 + (uint32_t)nrows;
+    __device__ __forceinline__ void finish() {
+        if (bulk.failed) {
+            // Drain the copies issued but not seen complete (bounded waits), so that no bulk copy
+            // still writes this warp's shared memory when the kernel returns.
+            for (int q = failed_q; q < fq; ++q) {
+                const uint32_t m = seq0 + (uint32_t)q;
+                mbar_wait(bulk.bars + 8 * (m % NS), (m / NS) & 1u);
+            }
+        }
+        bulk.seq = seq0 + (uint32_t)n;
+    }
+};
+
+// The forward's rows y0 .. y1-1 on an interior segment, staged by BulkGray.
+template <typename TI, int NS, typename Store>
+__device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                              const TI* ring, FwdBulk& bulk, Store&& store) {
+    BulkGray<TI, NS> src(a, bulk, ring, lane, x, y0 - 2, y1 - y0 + 4);  // gray rows y0-2 .. y1+1
+    fwd_strip_core<false, 1>(P, x, 0, a.H, y0, y1, [&](int, int, float g6[6]) { src.take(g6); }, store,
+                             [&] { return !bulk.failed; });
+    src.finish();
 }
 
 // Forward strips that write R: any segment (register staging) ...

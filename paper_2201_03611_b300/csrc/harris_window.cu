@@ -27,28 +27,43 @@ struct WindowArgs {
     float gh[kWinMaxK];
 };
 
-template <typename TI, typename TO, int K, bool EDGE, bool ALIGNED>
-__device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params& P, int lane, int x, int y0, int y1) {
-    const FwdArgs& a = wa.f;
-    constexpr int R = (K - 1) / 2;
-    constexpr int NA = K - 1;  // partial output rows in flight
-    const int H = a.H, W = a.W;
-    const RegRows<TI, EDGE, ALIGNED> rows(static_cast<const TI*>(a.img), a.img_pitch, x, W);
-    const int s_first = y0 - R > 0 ? y0 - R : 0;                 // Sobel rows used
-    const int g_first = s_first - 1;                              // gray rows g_first .. (clamped)
-    // gray staging: the next two rows are in flight in registers
-    int gnext = g_first;
+// Register staging of a warp's gray-row stream (rows g_first, g_first+1, ...; any segment and
+// alignment): the next two rows are in flight in registers.
+template <typename TI, bool EDGE, bool ALIGNED>
+struct RegGray {
+    const RegRows<TI, EDGE, ALIGNED> rows;
+    const int H, x, W;
+    int gnext;
     RawRow<TI> n0, n1;
-    rows.load(clampi(gnext, H), n0);
-    rows.load(clampi(gnext + 1, H), n1);
-    auto take_gray = [&](float g6[6]) {
+    __device__ __forceinline__ RegGray(const FwdArgs& a, int x_, int g_first)
+        : rows(static_cast<const TI*>(a.img), a.img_pitch, x_, a.W), H(a.H), x(x_), W(a.W), gnext(g_first) {
+        rows.load(clampi(gnext, H), n0);
+        rows.load(clampi(gnext + 1, H), n1);
+    }
+    __device__ __forceinline__ void take(float g6[6]) {
         float v[12];
         RegRows<TI, EDGE, ALIGNED>::unpack(n0, v);
         n0 = n1;
         rows.load(clampi(gnext + 2, H), n1);
         ++gnext;
         gray_row<EDGE>(v, g6, x, W);
-    };
+    }
+    __device__ __forceinline__ void finish() {}
+};
+
+// Output rows y0 .. y1-1 of a strip; src delivers the gray rows from max(y0 - r, 0) - 1 on.
+template <typename TO, int K, bool EDGE, typename Src>
+__device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params& P, int lane, int x, int y0, int y1,
+                                             Src& src) {
+    const FwdArgs& a = wa.f;
+    constexpr int R = (K - 1) / 2;
+    constexpr int NA = K - 1;  // partial output rows in flight
+    const int H = a.H, W = a.W;
+    const int s_first = y0 - R > 0 ? y0 - R : 0;  // first Sobel row used
+    auto take_gray = [&](float g6[6]) { src.take(g6); };
+    float gv[K], gh[K];  // window weights held in registers for the multiply-add chains
+#pragma unroll
+    for (int i = 0; i < K; ++i) { gv[i] = wa.gv[i]; gh[i] = wa.gh[i]; }
     StripRun st;
 #pragma unroll
     for (int j = 0; j < 4; ++j) st.P1[j] = st.P2[j] = make_float2(0.0f, 0.0f);
@@ -91,10 +106,10 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                done[c][j] = fmaf(wa.gv[K - 1], prod[c][j], vacc[0][c][j]);
+                done[c][j] = fmaf(gv[K - 1], prod[c][j], vacc[0][c][j]);
 #pragma unroll
-                for (int i = 0; i + 1 < NA; ++i) vacc[i][c][j] = fmaf(wa.gv[K - 2 - i], prod[c][j], vacc[i + 1][c][j]);
-                vacc[NA - 1][c][j] = fmaf(wa.gv[0], prod[c][j], 0.0f);
+                for (int i = 0; i + 1 < NA; ++i) vacc[i][c][j] = fmaf(gv[K - 2 - i], prod[c][j], vacc[i + 1][c][j]);
+                vacc[NA - 1][c][j] = fmaf(gv[0], prod[c][j], 0.0f);
             }
         if (p - (y0 - R) < K - 1) continue;
         const int y = p - R;
@@ -108,7 +123,7 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
             for (int j = 0; j < 4; ++j) {
                 float t = 0.0f;
 #pragma unroll
-                for (int b = 0; b < K; ++b) t = fmaf(wa.gh[b], e[j + b], t);
+                for (int b = 0; b < K; ++b) t = fmaf(gh[b], e[j + b], t);
                 S3[c][j] = t;
             }
         }
@@ -128,44 +143,83 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
     }
 }
 
-template <typename TI, typename TO, int K, bool ALIGNED>
+template <typename TI, typename TO, int K, bool ALIGNED, bool TMA>
 __global__ void __launch_bounds__(kFwdThreads, 2) harris_window_kernel(const __grid_constant__ WindowArgs wa) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const FwdArgs& a = wa.f;
+    constexpr int NS = kFwdBulkStages;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (kFwdThreads / 32) + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (kFwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;
+    FwdBulk bulk;
+    bulk.seq = 0;
+    bulk.failed = false;
+    TI* ring = nullptr;
+    if constexpr (TMA) {
+        ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
+        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdThreads * NS * 12 * sizeof(TI)) + warp * NS;
+        bulk.bars = smem_u32(bars);
+        if (lane == 0)
+            for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+        mbar_init_fence();
+        __syncwarp();
+    }
     Params P;
     load_params(P, a.wx, a.wy, a.kappa);
+    constexpr int R = (K - 1) / 2;
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
     warp_work(1, a.nseg, rows, a.nwarps, gw, lo, hi);
-    while (lo < hi) {
+    while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
         const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
         const int xb = a.x0 + seg * kSegOut;
         const int x = xb - 4 + 4 * lane;
         const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W);
-        if (edge) window_strip<TI, TO, K, true, ALIGNED>(wa, P, lane, x, a.ylo + r0, a.ylo + r1);
-        else window_strip<TI, TO, K, false, ALIGNED>(wa, P, lane, x, a.ylo + r0, a.ylo + r1);
+        const int y0 = a.ylo + r0, y1 = a.ylo + r1;
+        const int s_first = y0 - R > 0 ? y0 - R : 0;
+        const int s_last = y1 - 1 + R < a.H - 1 ? y1 - 1 + R : a.H - 1;
+        if (edge) {
+            RegGray<TI, true, ALIGNED> src(a, x, s_first - 1);
+            window_strip<TO, K, true>(wa, P, lane, x, y0, y1, src);
+        } else if constexpr (TMA) {
+            BulkGray<TI, NS> src(a, bulk, ring, lane, x, s_first - 1, s_last - s_first + 3);
+            window_strip<TO, K, false>(wa, P, lane, x, y0, y1, src);
+            src.finish();
+        } else {
+            RegGray<TI, false, ALIGNED> src(a, x, s_first - 1);
+            window_strip<TO, K, false>(wa, P, lane, x, y0, y1, src);
+        }
         lo += r1 - r0;
     }
+    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
 }
 
 template <typename TI, typename TO, int K>
 cudaError_t launch_window_k(WindowArgs& wa, cudaStream_t s) {
     FwdArgs& a = wa.f;
-    auto kern = a.aligned ? harris_window_kernel<TI, TO, K, true> : harris_window_kernel<TI, TO, K, false>;
+    constexpr int NS = kFwdBulkStages;
+    const bool tma = a.tma && a.aligned;
+    const size_t smem = tma ? (size_t)kFwdThreads * NS * 12 * sizeof(TI) + (kFwdThreads / 32) * NS * 8 : 0;
+    auto kern = tma ? harris_window_kernel<TI, TO, K, true, true>
+                    : (a.aligned ? harris_window_kernel<TI, TO, K, true, false>
+                                 : harris_window_kernel<TI, TO, K, false, false>);
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     if (units <= 0) return cudaSuccess;
+    if (tma) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFwdThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFwdThreads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t t = (int64_t)per_sm * sm_count() * (kFwdThreads / 32);
     t = std::min<int64_t>(t, std::max<int64_t>(1, units / kFwdMinRows));
     a.nwarps = (int)t;
     const int64_t blocks = (t + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
-    kern<<<(unsigned)blocks, kFwdThreads, 0, s>>>(wa);
+    kern<<<(unsigned)blocks, kFwdThreads, smem, s>>>(wa);
     return cudaPeekAtLastError();
 }
 
@@ -208,7 +262,7 @@ extern "C" shine_status shine_harris_window(const void* img, int64_t H, int64_t 
     const size_t chunk = si == 4 ? 16 : 8;
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.out_vec = aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
-    a.tma = 0;
+    a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
     a.err = nullptr;
     for (int i = 0; i < kWinMaxK; ++i) {
         wa.gv[i] = i < K ? gv[i] : 0.0f;
