@@ -317,6 +317,24 @@ SHINE_API shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, 
 SHINE_API shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda, shine_dtype dt, const float* x,
                                 float* y, void* stream);
 
+/*
+ * Bounded waits. Every wait of the kernels on a bulk copy polls its barrier a bounded number of
+ * times; a wait that gives up stops its warp's work (the results of that call are invalid) and
+ * sets a flag instead of hanging the GPU. Calls with a workspace (the backward passes) report it
+ * through shine_workspace_status; the forward, corner and window calls set one library-wide
+ * flag per GPU, read (and cleared when clear != 0) by shine_wait_status. Both synchronise with
+ * the device.
+ */
+SHINE_API shine_status shine_wait_status(int* failed, int clear);
+
+/*
+ * Self-test of the bounded-wait path (no counterpart in the paper): launches one warp that
+ * waits, with at most max_spins polls (1 .. 2^22), on a shared-memory barrier that nothing
+ * completes, and writes 1 to *result (a device int) when the wait gave up -- as it must -- and
+ * 0 otherwise. No fault is involved; the context stays usable. Asynchronous on stream.
+ */
+SHINE_API shine_status shine_selftest_bounded_wait(int32_t max_spins, int* result, void* stream);
+
 /* Static description of a status code. */
 SHINE_API const char* shine_status_string(shine_status s);
 

@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
         "shine_pipeline_host_workspace": (st, [i64, i64, f, i32, ctypes.POINTER(sz)]),
         "shine_pipeline_host": (st, [p, p, p, p, i64, i64, f, f, p, p, p, p, p, p, p, p, p, sz, i32, p]),
         "shine_mv": (st, [p, i64, i64, i64, f, p, p, p]),
+        "shine_wait_status": (st, [ctypes.POINTER(f), f]),
+        "shine_selftest_bounded_wait": (st, [i32, p, p]),
         "shine_iterate_sum": (st, [p, i64, i32, i32, p, p]),
         "shine_stencil2d": (st, [p, i64, i64, i64, f, f, i32, p, p, p, p, i64, f, p]),
         "shine_harris_window": (st, [p, i64, i64, i64, f, p, p, p, i32, p, p, p, i64, f, p]),

@@ -1,7 +1,10 @@
 // extern "C" entry points of libshine (declared in include/shine.h): argument validation on
 // the host, the work decomposition, and the kernel launches. Nothing here allocates device
-// memory except shine_plan_create (in batched.cu), and nothing synchronises.
+// memory except shine_plan_create (in batched.cu), and nothing synchronises except the two
+// status queries (shine_workspace_status, shine_wait_status).
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include <algorithm>
 #include <cstdint>
@@ -15,6 +18,13 @@ namespace shine {
 
 thread_local int g_last_cuda_error = 0;
 
+// Set (atomically, to 1) by a kernel launched without a workspace -- the forward, corner and
+// window kernels -- when one of its bounded waits gives up; read and cleared by
+// shine_wait_status. One word per GPU that loads the library.
+__device__ unsigned int g_wait_flag;
+std::mutex g_wait_mutex;
+unsigned int* g_wait_ptr[64] = {};
+
 shine_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SHINE_OK;
     g_last_cuda_error = (int)e;
@@ -24,6 +34,18 @@ shine_status cuda_status(cudaError_t e) {
 size_t dtype_size(int dt) { return dt == SHINE_F32 ? 4 : 2; }
 bool dtype_ok(int dt) { return dt == SHINE_F32 || dt == SHINE_BF16 || dt == SHINE_F16; }
 bool border_ok(int b) { return b == SHINE_VALID || b == SHINE_CLAMP; }
+
+unsigned int* wait_flag() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_wait_mutex);
+    if (g_wait_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_wait_flag) != cudaSuccess) return nullptr;
+        g_wait_ptr[dev] = static_cast<unsigned int*>(p);
+    }
+    return g_wait_ptr[dev];
+}
 
 int sm_count() {
     int dev = 0;
@@ -100,6 +122,20 @@ const char* shine_status_string(shine_status s) {
 
 int shine_last_cuda_error(void) { return g_last_cuda_error; }
 
+shine_status shine_wait_status(int* failed, int clear) {
+    if (!failed) return SHINE_ERR_INVALID_ARG;
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_wait_flag, sizeof v);
+    if (e != cudaSuccess) return cuda_status(e);
+    *failed = v != 0;
+    if (clear) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_wait_flag, &zero, sizeof zero);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SHINE_OK;
+}
+
 shine_status shine_workspace_status(const void* workspace, int* failed) {
     if (!workspace || !failed) return SHINE_ERR_INVALID_ARG;
     unsigned int v = 0;
@@ -141,7 +177,7 @@ shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t i
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.out_vec = border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
     a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
-    a.err = nullptr;
+    a.err = wait_flag();
     return cuda_status(launch_harris_fwd(a, dt, out_dt, static_cast<cudaStream_t>(stream)));
 }
 
@@ -169,7 +205,7 @@ shine_status shine_corners(const void* img, int64_t H, int64_t W, int64_t img_pi
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.out_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
     a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
-    a.err = nullptr;
+    a.err = wait_flag();
     c.mask = mask;
     c.mask_pitch = mask_pitch;
     c.threshold = threshold;

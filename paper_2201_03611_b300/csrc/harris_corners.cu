@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
         if (ye == y1 && !bulk.failed) emit(y1 - 1, ha);  // the region's last row: nothing below it
         lo += r1 - r0;
     }
+    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
 }
 
 template <typename TI, typename TO>

@@ -263,7 +263,7 @@ extern "C" shine_status shine_harris_window(const void* img, int64_t H, int64_t 
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
     a.out_vec = aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
     a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
-    a.err = nullptr;
+    a.err = wait_flag();
     for (int i = 0; i < kWinMaxK; ++i) {
         wa.gv[i] = i < K ? gv[i] : 0.0f;
         wa.gh[i] = i < K ? gh[i] : 0.0f;

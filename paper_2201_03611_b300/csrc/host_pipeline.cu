@@ -159,7 +159,7 @@ shine_status shine_pipeline_host(const void* img_h, const void* gout_h, void* ou
             f.aligned = (img_row % (si == 4 ? 16 : 8)) == 0;  // vector staging needs aligned rows
             f.out_vec = border == SHINE_CLAMP && (Wo * si) % (4 * si) == 0;
             f.tma = SHINE_FWD_TMA && (img_row % 16) == 0;
-            f.err = nullptr;
+            f.err = wait_flag();
             SHINE_TRY(launch_harris_fwd(f, dt, dt, ds->comp));
         }
         BwdArgs a;

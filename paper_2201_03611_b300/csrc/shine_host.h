@@ -16,6 +16,8 @@ size_t dtype_size(int dt);
 bool dtype_ok(int dt);
 bool border_ok(int b);
 int sm_count();
+// Device address of the library's bounded-wait failure flag on the current device (or null).
+unsigned int* wait_flag();
 shine_status check_shape(int64_t H, int64_t W, int border);
 bool aligned_to(const void* p, size_t a);
 void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows);

@@ -78,6 +78,14 @@ def workspace_failed(workspace: torch.Tensor) -> bool:
     return bool(f.value)
 
 
+def wait_failed(clear: bool = True) -> bool:
+    """True when a bounded wait of a forward, corner or window call on the current GPU gave up
+    since the last clear (those results are invalid). Synchronises with the device."""
+    f = ctypes.c_int()
+    L.check(L.lib().shine_wait_status(ctypes.byref(f), 1 if clear else 0), "shine_wait_status")
+    return bool(f.value)
+
+
 def _row_pitch(t: torch.Tensor) -> int:
     return t.stride(0)
 
