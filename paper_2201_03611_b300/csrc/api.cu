@@ -82,7 +82,7 @@ void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_imag
 Geometry fwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
     fill_geometry(g, H, W, border, false, (int)H);
-    g.x0 = kSegmentOrigin;
+    g.x0 = kFwdSegmentOrigin;
     g.nseg = (g.xhi - g.x0 + kSegOut - 1) / kSegOut;
     return g;
 }
@@ -90,7 +90,7 @@ Geometry fwd_geometry(int64_t H, int64_t W, int border) {
 Geometry bwd_geometry(int64_t H, int64_t W, int border) {
     Geometry g;
     fill_geometry(g, H, W, border, true, (int)H);
-    g.x0 = kSegmentOrigin;
+    g.x0 = kBwdSegmentOrigin;
     g.nseg = (g.xhi - g.x0 + kSegOut - 1) / kSegOut;
     return g;
 }

@@ -149,12 +149,23 @@ constexpr int kFwdMinRows = 16;  // minimum rows per warp slice
 constexpr int kBwdMinRows = 32;
 constexpr int kMaxWarpsPerSm = 64;
 constexpr size_t kWorkspaceHeader = 256;  // backward workspace: error word, then the partial sums
-// First output column of segment 0 (the single-image kernels): segment s outputs columns
-// 120 s - 116 .. 120 s + 3 and stages from column 120 (s - 1), so every interior segment's
-// staged span starts on a 16-byte boundary for float32 and 16-bit rows and cotangents alike,
-// which bulk copies require. (Origin -4 also aligns the spans and saves the nearly empty
-// segment 0, but measured 7-8% slower on 8192^2 for both passes.)
-constexpr int kSegmentOrigin = -116;
+// First output column of segment 0 in the single-image kernels, per pass. Any origin = 4
+// (mod 8) makes every interior segment's staged span (4 columns left of its output) start on
+// an 8-pixel boundary, i.e. a 16-byte boundary for float32 and 16-bit rows and cotangents alike,
+// which bulk copies require. Which of them is fastest depends on how the spans fall on the
+// memory system; chosen by sweeps of -116 .. -12 on 2048^2 .. 8192^2 (forward: -108, 11% faster than
+// -116 in bf16, equal in float32; adjoint: -76, 1-2% faster).
+#ifndef SHINE_FWD_SEGMENT_ORIGIN
+#define SHINE_FWD_SEGMENT_ORIGIN -108
+#endif
+#ifndef SHINE_BWD_SEGMENT_ORIGIN
+#define SHINE_BWD_SEGMENT_ORIGIN -76
+#endif
+constexpr int kFwdSegmentOrigin = SHINE_FWD_SEGMENT_ORIGIN;
+constexpr int kBwdSegmentOrigin = SHINE_BWD_SEGMENT_ORIGIN;
+static_assert(((kFwdSegmentOrigin % 8) + 8) % 8 == 4 && ((kBwdSegmentOrigin % 8) + 8) % 8 == 4,
+              "segment spans must start on 8-pixel boundaries");
+static_assert(kFwdSegmentOrigin > -120 && kBwdSegmentOrigin > -120, "segment 0 must reach column 0");
 // out[f] = sum over n partials[f * n + i] (fixed order, float64), f < kParamSlots; any out
 // pointer may be NULL.
 cudaError_t launch_finalize_params(const double* partials, int64_t n, float* gkappa, float* gwx,

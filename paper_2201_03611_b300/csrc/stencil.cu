@@ -262,7 +262,7 @@ extern "C" shine_status shine_stencil2d(const void* in, int64_t H, int64_t W, in
     } else {
         a.xlo = 0; a.xhi = (int)W; a.ylo = 0; a.yhi = (int)H; a.ox = 0; a.oy = 0;
     }
-    a.x0 = kSegmentOrigin;  // interior segments' lane columns are multiples of 4
+    a.x0 = kFwdSegmentOrigin;  // interior segments' lane columns are multiples of 4
     a.nseg = (a.xhi - a.x0 + kSegOut - 1) / kSegOut;
     a.nwarps = 0;
     a.aligned = aligned_to(in, 4 * si) && ((size_t)in_pitch * si) % (4 * si) == 0;
