@@ -114,3 +114,84 @@ def test_dkappa_closed_form():
     t2 = PINS.library_harris(img, 0.0, wx.double(), wy.double(), "clamp") - \
         PINS.library_harris(img, 1.0, wx.double(), wy.double(), "clamp")
     assert abs(gk - float(-(g.double().numpy() * t2).sum())) <= 1e-10 * abs(gk)
+
+
+def _direct_harris(img, kappa, wx, wy, border):
+    """R by direct nested loops over each output's 5 x 5 footprint, written from the stage
+    definitions (gray, 3x3 correlation, products, 3x3 box, det - kappa trace^2) with the clamp
+    of each stage applied to the index it reads -- no patterns, no intermediate arrays."""
+    h, w = len(img), len(img[0])
+    clamp = border == "clamp"
+    cy = (lambda y: min(max(y, 0), h - 1)) if clamp else (lambda y: y)
+    cx = (lambda x: min(max(x, 0), w - 1)) if clamp else (lambda x: x)
+
+    def gray(y, x):
+        p = img[y][x]
+        return 0.299 * p[0] + 0.587 * p[1] + 0.114 * p[2]
+
+    def grad(y, x):  # Sobel at (y, x); its 3x3 reads clamp at the gray stage
+        ix = iy = 0.0
+        for a in range(3):
+            for b in range(3):
+                g = gray(cy(y + a - 1), cx(x + b - 1))
+                ix += wx[a][b] * g
+                iy += wy[a][b] * g
+        return ix, iy
+
+    out = []
+    ys = range(h) if clamp else range(2, h - 2)
+    xs = range(w) if clamp else range(2, w - 2)
+    for y in ys:
+        row = []
+        for x in xs:
+            sxx = sxy = syy = 0.0
+            for a in (-1, 0, 1):
+                for b in (-1, 0, 1):
+                    ix, iy = grad(cy(y + a), cx(x + b))   # the products clamp at their own stage
+                    sxx += ix * ix
+                    sxy += ix * iy
+                    syy += iy * iy
+            row.append(sxx * syy - sxy * sxy - kappa * (sxx + syy) ** 2)
+        out.append(row)
+    return out
+
+
+@pytest.mark.parametrize("shape,border", [((1, 1), "clamp"), ((3, 4), "clamp"), ((7, 9), "clamp"),
+                                          ((16, 16), "clamp"), ((12, 5), "clamp"), ((5, 5), "valid"),
+                                          ((16, 13), "valid")])
+def test_brute_force_direct_formula(shape, border):
+    """The pattern oracle equals a direct 5x5-footprint nested-loop formula (no patterns)."""
+    h, w = shape
+    img = wl.random_image(h, w, seed=h * 31 + w).double().tolist()
+    wx, wy = [t.double().tolist() for t in wl.random_weights(h + 2 * w)]
+    a = np.array(H.harris(img, 0.06, wx, wy, border))
+    b = np.array(_direct_harris(img, 0.06, wx, wy, border))
+    assert a.shape == b.shape
+    assert np.max(np.abs(a - b)) <= 1e-13 * max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("border", ["clamp", "valid"])
+def test_adjoint_dot_product_with_a_forward_difference_jvp(border):
+    """<J v, g> = <v, J^T g>: the reverse pass of the pattern oracle against a central-difference
+    directional derivative of its forward pass, for a direction in the image and in every
+    parameter at once."""
+    h, w = 8, 9
+    img = wl.random_image(h, w, seed=5).double().numpy()
+    wx, wy = [t.double().numpy() for t in wl.random_weights(5)]
+    kappa = 0.05
+    rng = np.random.default_rng(6)
+    v_img, v_k = rng.standard_normal(img.shape), rng.standard_normal()
+    v_wx, v_wy = rng.standard_normal((3, 3)), rng.standard_normal((3, 3))
+    ho, wo = (h, w) if border == "clamp" else (h - 4, w - 4)
+    g = rng.standard_normal((ho, wo))
+
+    def R(t):
+        return np.array(H.harris((img + t * v_img).tolist(), kappa + t * v_k, (wx + t * v_wx).tolist(),
+                                 (wy + t * v_wy).tolist(), border))
+    eps = 1e-5
+    jvp = (R(eps) - R(-eps)) / (2 * eps)
+    lhs = float(np.sum(jvp * g))
+    d_img, d_k, d_wx, d_wy = H.harris_vjp(img.tolist(), kappa, wx.tolist(), wy.tolist(), border, g.tolist())
+    rhs = float(np.sum(np.array(d_img) * v_img) + d_k * v_k + np.sum(np.array(d_wx) * v_wx)
+                + np.sum(np.array(d_wy) * v_wy))
+    assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(rhs))
