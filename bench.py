@@ -157,7 +157,7 @@ def job_throughput(pixels_per_rank_step: int, steps: int, world: int, max_ms: fl
     return world * pixels_per_rank_step * steps / (max_ms * 1e-3) / 1e9
 
 
-def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: int) -> dict:
+def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: int, single_core_rows: int = 0) -> dict:
     """The FP64 C oracle (as it stands) on a band of the workload: forward + reverse pass."""
     from oracle import cref
     wx, wy = wl.sobel_weights()
@@ -169,9 +169,31 @@ def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: in
     cref.backward(band, gb, kappa, wx, wy, "clamp")
     dt = time.perf_counter() - t0
     px = band.shape[0] * band.shape[1]
-    return {"value": px / dt / 1e9, "unit": "Gpixel/s", "cores": cref.num_threads(), "kind": "oracle",
-            "sample": f"FP64 C oracle, forward + reverse pass over rows 0..{rows - 1} of the "
-                      f"{img.shape[0]}x{img.shape[1]} image as a CLAMP image ({px} px, {dt:.2f} s)"}
+    cores = cref.num_threads()
+    out = {"value": px / dt / 1e9, "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
+           "sample": f"FP64 C oracle, forward + reverse pass over rows 0..{rows - 1} of the "
+                     f"{img.shape[0]}x{img.shape[1]} image as a CLAMP image ({px} px, {dt:.2f} s)",
+           "cpu_model": _cpu_model()}
+    if single_core_rows > 0:
+        b1, g1 = img[:single_core_rows].contiguous(), g[:single_core_rows].contiguous()
+        t0 = time.perf_counter()
+        cref.forward(b1, kappa, wx, wy, "clamp", nthreads=1)
+        cref.backward(b1, g1, kappa, wx, wy, "clamp", nthreads=1)
+        d1 = time.perf_counter() - t0
+        cref.forward(b1[:1].contiguous(), kappa, wx, wy, "clamp", nthreads=cores)  # restore the thread count
+        out["one_core"] = {"value": b1.shape[0] * b1.shape[1] / d1 / 1e9, "unit": "Gpixel/s",
+                           "sample": f"rows 0..{single_core_rows - 1}, 1 thread ({d1:.2f} s)"}
+    return out
+
+
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_ours(args, world, rank, local) -> dict | None:
@@ -285,7 +307,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(img_h, g_h, kappa, rows=args.cpu_rows)
+        line["cpu_baseline"] = cpu_oracle_sample(img_h, g_h, kappa, rows=args.cpu_rows, single_core_rows=128)
     if world == 1 and not args.no_extras:
         del img, g, out, gimg, ws, img_pin, g_pin, out_pin, gimg_pin, hws
         torch.cuda.empty_cache()
