@@ -299,6 +299,17 @@ SHINE_API shine_status shine_stencil2d(const void* in, int64_t H, int64_t W, int
 SHINE_API shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, int32_t k, float* out, void* stream);
 
 /*
+ * The same iterate with the body split(n) >> map(reduce(op, identity)): op SHINE_REDUCE_SUM
+ * (+ from 0; shine_iterate_sum), SHINE_REDUCE_MAX (max from -inf) or SHINE_REDUCE_MIN (min from
+ * +inf). max and min are IEEE maxNum / minNum (a NaN operand is ignored unless both are NaN) and
+ * exact, so their results do not depend on the grouping. Arguments, limits and errors as
+ * shine_iterate_sum; an unknown op -> SHINE_ERR_INVALID_ARG.
+ */
+typedef enum { SHINE_REDUCE_SUM = 0, SHINE_REDUCE_MAX = 1, SHINE_REDUCE_MIN = 2 } shine_reduce_op;
+SHINE_API shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t n, int32_t k, shine_reduce_op op,
+                                            float* out, void* stream);
+
+/*
  * Matrix-vector multiply, the paper's running example (Sec. 4, MV):
  *   y[i] = reduce(+, 0)(map(*)(zip(A[i], x)))  =  sum_j A[i][j] * x[j]
  *   A      [M][lda] elements of type dt, row-major, lda >= max(N, 1) (device)

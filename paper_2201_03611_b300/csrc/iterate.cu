@@ -1,6 +1,7 @@
-// iterate with double buffering (Sec. 6): k rounds of the body split(n) >> map(reduce(+, 0))
-// over Array[(n^k) m], each round summing every n consecutive values (a left fold from 0), so
-// out[j] is the level-by-level tree sum of in[j n^k .. (j+1) n^k).
+// iterate with double buffering (Sec. 6): k rounds of the body split(n) >> map(reduce(op, id))
+// over Array[(n^k) m], each round folding every n consecutive values from the left, starting
+// at the operator's identity (+ from 0, max from -inf, min from +inf), so out[j] is the
+// level-by-level tree reduction of in[j n^k .. (j+1) n^k).
 //
 // A CTA takes G whole output groups at a time (G n^(k-1) <= kIterBuf). Round 0 reads the input
 // straight from global memory (the double buffer's first input is the overall input, no copy)
@@ -25,37 +26,56 @@ constexpr int kIterThreads = 256;
 constexpr int kIterBuf = 6144;  // floats per shared-memory buffer (two buffers: 48 KB)
 constexpr int kIterUnroll = 4;  // round-0 values a thread has in flight
 
-// Left fold of n consecutive values from 0 (N > 0: n == N known at compile time, so all its
-// loads are issued together).
-template <int N>
+// The fold operator: + (rounded to nearest), max or min (IEEE maxNum / minNum: a NaN operand is
+// ignored unless both are NaN), with its identity.
+template <int OP> struct FoldOp;
+template <> struct FoldOp<SHINE_REDUCE_SUM> {
+    __device__ static float id() { return 0.0f; }
+    __device__ static float f(float a, float b) { return __fadd_rn(a, b); }
+};
+template <> struct FoldOp<SHINE_REDUCE_MAX> {
+    __device__ static float id() { return __int_as_float(0xff800000); }
+    __device__ static float f(float a, float b) { return fmaxf(a, b); }
+};
+template <> struct FoldOp<SHINE_REDUCE_MIN> {
+    __device__ static float id() { return __int_as_float(0x7f800000); }
+    __device__ static float f(float a, float b) { return fminf(a, b); }
+};
+
+// Left fold of n consecutive values from the identity (N > 0: n == N known at compile time, so
+// all its loads are issued together).
+template <int N, int OP>
 __device__ __forceinline__ float fold_global(const float* __restrict__ p, int n) {
-    float s = 0.0f;
+    using F = FoldOp<OP>;
+    float s = F::id();
     if constexpr (N > 0 && N % 4 == 0) {
         float4 v[N / 4];
 #pragma unroll
         for (int e = 0; e < N / 4; ++e) v[e] = __ldcs(reinterpret_cast<const float4*>(p) + e);  // streamed once
 #pragma unroll
-        for (int e = 0; e < N / 4; ++e) s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(s, v[e].x), v[e].y), v[e].z), v[e].w);
+        for (int e = 0; e < N / 4; ++e) s = F::f(F::f(F::f(F::f(s, v[e].x), v[e].y), v[e].z), v[e].w);
     } else if constexpr (N > 0) {
         float v[N];
 #pragma unroll
         for (int e = 0; e < N; ++e) v[e] = __ldcs(p + e);
 #pragma unroll
-        for (int e = 0; e < N; ++e) s = __fadd_rn(s, v[e]);
+        for (int e = 0; e < N; ++e) s = F::f(s, v[e]);
     } else {
-        for (int e = 0; e < n; ++e) s = __fadd_rn(s, __ldcs(p + e));
+        for (int e = 0; e < n; ++e) s = F::f(s, __ldcs(p + e));
     }
     return s;
 }
 
+template <int OP>
 __device__ __forceinline__ float fold_shared(const float* p, int n) {
-    float s = 0.0f;
-    for (int e = 0; e < n; ++e) s = __fadd_rn(s, p[e]);
+    using F = FoldOp<OP>;
+    float s = F::id();
+    for (int e = 0; e < n; ++e) s = F::f(s, p[e]);
     return s;
 }
 
-template <int N>
-__global__ void __launch_bounds__(kIterThreads) iterate_sum_kernel(const float* __restrict__ in, int64_t m, int n,
+template <int N, int OP>
+__global__ void __launch_bounds__(kIterThreads) iterate_kernel(const float* __restrict__ in, int64_t m, int n,
                                                                    int k, int64_t span1, int64_t G,
                                                                    float* __restrict__ out) {
     // span1 = n^(k-1): level-1 values per output group; G groups per pass (G * span1 <= kIterBuf)
@@ -74,7 +94,7 @@ __global__ void __launch_bounds__(kIterThreads) iterate_sum_kernel(const float* 
 #pragma unroll
             for (int u = 0; u < kIterUnroll; ++u) {
                 const int64_t v = v0 + (int64_t)u * kIterThreads;
-                r[u] = v < count ? fold_global<N>(src0 + v * n, n) : 0.0f;
+                r[u] = v < count ? fold_global<N, OP>(src0 + v * n, n) : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < kIterUnroll; ++u) {
@@ -88,23 +108,36 @@ __global__ void __launch_bounds__(kIterThreads) iterate_sum_kernel(const float* 
             const float* src = buf[(i - 1) & 1];
             float* dst = i == k - 1 ? out + g0 : buf[i & 1];
             count /= n;
-            for (int64_t v = threadIdx.x; v < count; v += kIterThreads) dst[v] = fold_shared(src + v * n, n);
+            for (int64_t v = threadIdx.x; v < count; v += kIterThreads) dst[v] = fold_shared<OP>(src + v * n, n);
         }
         __syncthreads();  // the buffers are reused by the next pass
     }
 }
 
-template <int N>
+template <int N, int OP>
 cudaError_t launch_iterate(const float* in, int64_t m, int n, int k, int64_t span1, int64_t G, float* out,
                            cudaStream_t s) {
     const int64_t passes = (m + G - 1) / G;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_sum_kernel<N>, kIterThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_kernel<N, OP>, kIterThreads, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(passes, (int64_t)per_sm * sm_count()));
-    iterate_sum_kernel<N><<<(unsigned)blocks, kIterThreads, 0, s>>>(in, m, n, k, span1, G, out);
+    iterate_kernel<N, OP><<<(unsigned)blocks, kIterThreads, 0, s>>>(in, m, n, k, span1, G, out);
     return cudaPeekAtLastError();
+}
+
+// Round 0 reads groups of n consecutive floats: with 16-byte loads when n is a multiple of 4
+// and the input is 16-byte aligned.
+template <int OP>
+cudaError_t launch_iterate_op(const float* in, int64_t m, int n, int k, int64_t span1, int64_t G, float* out,
+                              cudaStream_t s) {
+    const bool vec = aligned_to(in, 16);
+    if (n == 2) return launch_iterate<2, OP>(in, m, n, k, span1, G, out, s);
+    if (n == 4 && vec) return launch_iterate<4, OP>(in, m, n, k, span1, G, out, s);
+    if (n == 8 && vec) return launch_iterate<8, OP>(in, m, n, k, span1, G, out, s);
+    if (n == 16 && vec) return launch_iterate<16, OP>(in, m, n, k, span1, G, out, s);
+    return launch_iterate<0, OP>(in, m, n, k, span1, G, out, s);
 }
 
 }  // namespace
@@ -112,9 +145,10 @@ cudaError_t launch_iterate(const float* in, int64_t m, int n, int k, int64_t spa
 
 using namespace shine;
 
-extern "C" shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, int32_t k, float* out,
-                                          void* stream) {
+extern "C" shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t n, int32_t k, shine_reduce_op op,
+                                             float* out, void* stream) {
     if (m < 0 || n < 1 || k < 0) return SHINE_ERR_INVALID_ARG;
+    if (op != SHINE_REDUCE_SUM && op != SHINE_REDUCE_MAX && op != SHINE_REDUCE_MIN) return SHINE_ERR_INVALID_ARG;
     // n^k and n^(k-1) without overflow
     int64_t span = 1, span1 = 1;
     for (int i = 0; i < k; ++i) {
@@ -131,14 +165,14 @@ extern "C" shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n,
         return cuda_status(cudaMemcpyAsync(out, in, (size_t)m * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (k > 1 && span1 > kIterBuf) return SHINE_ERR_UNSUPPORTED;  // one group's level-1 values must fit
     const int64_t G = k > 1 ? kIterBuf / span1 : kIterBuf;
-    // Round 0 reads groups of n consecutive floats: with 16-byte loads when n is a multiple of 4
-    // and the input is 16-byte aligned.
-    const bool vec = aligned_to(in, 16);
     cudaError_t e;
-    if (n == 2) e = launch_iterate<2>(in, m, n, k, span1, G, out, s);
-    else if (n == 4 && vec) e = launch_iterate<4>(in, m, n, k, span1, G, out, s);
-    else if (n == 8 && vec) e = launch_iterate<8>(in, m, n, k, span1, G, out, s);
-    else if (n == 16 && vec) e = launch_iterate<16>(in, m, n, k, span1, G, out, s);
-    else e = launch_iterate<0>(in, m, n, k, span1, G, out, s);
+    if (op == SHINE_REDUCE_SUM) e = launch_iterate_op<SHINE_REDUCE_SUM>(in, m, n, k, span1, G, out, s);
+    else if (op == SHINE_REDUCE_MAX) e = launch_iterate_op<SHINE_REDUCE_MAX>(in, m, n, k, span1, G, out, s);
+    else e = launch_iterate_op<SHINE_REDUCE_MIN>(in, m, n, k, span1, G, out, s);
     return cuda_status(e);
+}
+
+extern "C" shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, int32_t k, float* out,
+                                          void* stream) {
+    return shine_iterate_reduce(in, m, n, k, SHINE_REDUCE_SUM, out, stream);
 }

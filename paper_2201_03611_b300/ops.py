@@ -230,9 +230,13 @@ def mv(A: torch.Tensor, x: torch.Tensor, out=None) -> torch.Tensor:
     return out
 
 
-def iterate_sum(x: torch.Tensor, n: int, k: int, out=None) -> torch.Tensor:
-    """iterate(k, split(n) >> map(reduce(+, 0))) of a contiguous float32 CUDA vector of length
-    (n^k) m (shine_iterate_sum); returns the m tree sums."""
+_REDUCE = {"sum": 0, "max": 1, "min": 2}
+
+
+def iterate_sum(x: torch.Tensor, n: int, k: int, out=None, op: str = "sum") -> torch.Tensor:
+    """iterate(k, split(n) >> map(reduce(op, identity))) of a contiguous float32 CUDA vector of
+    length (n^k) m (shine_iterate_reduce; op "sum", "max" or "min"); returns the m tree
+    reductions."""
     if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 1 or not x.is_contiguous():
         raise ValueError("x must be a contiguous 1-D float32 CUDA tensor")
     span = n ** k
@@ -243,7 +247,10 @@ def iterate_sum(x: torch.Tensor, n: int, k: int, out=None) -> torch.Tensor:
         out = torch.empty(m, device=x.device, dtype=torch.float32)
     if out.shape != (m,) or out.dtype != torch.float32 or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous float32 tensor of shape ({m},)")
-    L.check(L.lib().shine_iterate_sum(_ptr(x), m, n, k, _ptr(out), _stream(x.device)), "shine_iterate_sum")
+    if op not in _REDUCE:
+        raise ValueError(f"op must be one of {sorted(_REDUCE)}")
+    L.check(L.lib().shine_iterate_reduce(_ptr(x), m, n, k, _REDUCE[op], _ptr(out), _stream(x.device)),
+            "shine_iterate_reduce")
     return out
 
 

@@ -70,3 +70,19 @@ def test_iterate_sum_full_size_sampled(shine):
     x = wl.iterate_inputs(m, n, k, seed=0)
     y = shine.iterate_sum(x.cuda(), n, k).cpu().numpy()
     assert np.array_equal(y, IT.iterate_sum_np(x.numpy(), n, k, np.float32))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+@pytest.mark.parametrize("m,n,k", [(5, 2, 3), (1000, 4, 5), (33, 3, 4), (2, 4, 7), (6145, 4, 1)])
+def test_iterate_max_min_match_oracle(shine, op, m, n, k):
+    """max / min folds are exact: the kernel equals the oracle bit for bit, whatever the order."""
+    x = wl.iterate_inputs(m, n, k, seed=m + n + k)
+    y = shine.iterate_sum(x.cuda(), n, k, op=op).cpu().numpy()
+    assert np.array_equal(y, IT.iterate_fold_np(x.numpy(), n, k, op, np.float32))
+
+
+def test_iterate_max_ignores_nan_operands(shine):
+    x = torch.tensor([1.0, float("nan"), -2.0, 0.5, float("nan"), float("nan"), 3.0, -1.0])
+    y = shine.iterate_sum(x.cuda(), 2, 2, op="max").cpu().numpy()
+    assert np.array_equal(y, IT.iterate_fold_np(x.numpy(), 2, 2, "max", np.float32))
+    assert y[0] == 1.0 and y[1] == 3.0

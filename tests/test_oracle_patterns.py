@@ -198,3 +198,20 @@ def test_iterate_sum_forms_agree_and_fix_the_tree():
     left = IT.iterate_sum_np(x32, 4, 1, np.float32)[0]
     assert left == np.float32(1.0)                       # ((1 + e) + e) + e rounds back to 1
     assert IT.iterate_sum_np(x32, 2, 2, np.float32)[0] == np.float32(1.0) + np.float32(2.0 ** -23)
+
+
+def test_iterate_max_and_min_forms_agree_and_equal_the_group_extrema():
+    """Sec. 6 with max / min bodies: the list form and the numpy form agree exactly, each output
+    is its group's extremum, and a NaN operand is ignored (maxNum / minNum)."""
+    from oracle import iterate_sum as IT
+    rng = np.random.default_rng(8)
+    for n, k, m in ((2, 3, 5), (3, 2, 4), (4, 1, 3)):
+        x = rng.standard_normal(n ** k * m)
+        for op, ref in (("max", np.max), ("min", np.min)):
+            a = IT.iterate_fold(x.tolist(), n, k, op)
+            b = IT.iterate_fold_np(x, n, k, op)
+            assert np.array_equal(np.array(a), b)
+            assert np.array_equal(b, ref(x.reshape(m, -1), axis=1))
+    x = np.array([1.0, np.nan, -2.0, 0.5])
+    assert IT.iterate_fold(x.tolist(), 2, 2, "max") == [1.0]
+    assert IT.iterate_fold_np(x, 2, 2, "min")[0] == -2.0
