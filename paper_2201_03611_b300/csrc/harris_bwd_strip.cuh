@@ -215,8 +215,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     // One step: stage image row r = r_first + s and cotangent row r-2, then B1..B6 for the rows
     // whose inputs are complete. FAST steps are those whose rows are all interior to the image
-    // and to this strip (no clamp, fold or ownership test is needed); they run back to back in
-    // threes, so the 3-row windows rotate by renaming instead of register moves.
+    // and to this strip (no clamp, fold or ownership test is needed).
     auto step = [&](auto fast_tag, int s) {
         constexpr bool FAST = decltype(fast_tag)::value;
         const int r = r_first + s;
@@ -440,25 +439,13 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
     const int s_a = 8 + (y0 < 2 ? 2 - y0 : 0);
     const int s_b = (y1 - 3 < H - 5 ? y1 - 3 : H - 5) - y0 + 9;  // exclusive
     int s = 2, since_flush = 0;
-    for (; s < nrows && s < s_a; ++s) {
-        if (TMA && bulk->failed) break;
-        step(general, s);
-        if (++since_flush == kFlushRows) { flush(); since_flush = 0; }
-    }
+    // One loop with one copy of each step kind (the general steps at the strip's two ends, the
+    // fast ones between), to keep the code the warps run small.
 #pragma unroll 1
-    for (; s + SHINE_BWD_FAST_UNROLL <= s_b; s += SHINE_BWD_FAST_UNROLL) {
-        if (TMA && bulk->failed) break;
-        step(fast, s);
-        if (SHINE_BWD_FAST_UNROLL == 3) {
-            step(fast, s + 1);
-            step(fast, s + 2);
-        }
-        since_flush += SHINE_BWD_FAST_UNROLL;
-        if (since_flush >= kFlushRows) { flush(); since_flush = 0; }
-    }
     for (; s < nrows; ++s) {
         if (TMA && bulk->failed) break;
-        step(general, s);
+        if (s >= s_a && s < s_b) step(fast, s);
+        else step(general, s);
         if (++since_flush == kFlushRows) { flush(); since_flush = 0; }
     }
     acc[0] += partk;

@@ -26,9 +26,6 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_BWD_STAGES
 #define SHINE_BWD_STAGES 8        // staged rows of the backward ring
 #endif
-#ifndef SHINE_BWD_FAST_UNROLL
-#define SHINE_BWD_FAST_UNROLL 1   // backward fast steps per loop iteration (1 or 3)
-#endif
 #ifndef SHINE_BWD_TMA
 #define SHINE_BWD_TMA 1           // backward interior segments staged by bulk copies
 #endif
