@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
             const int y0 = a.ylo + band * a.band_rows, y1 = min(y0 + a.band_rows, a.yhi);
             const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > W) || a.valid;
             if (a.aligned) {
-                if (edge) fwd_strip<T, T, kFwdStages, true, true>(a, P, lane, x, y0, y1);
+                if (edge) fwd_strip<T, T, kFwdEdgeStages, true, true>(a, P, lane, x, y0, y1);
                 else fwd_strip<T, T, kFwdStages, false, true>(a, P, lane, x, y0, y1);
             } else {
                 fwd_strip<T, T, kFwdStages, true, false>(a, P, lane, x, y0, y1);

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
                 cen[j] = r[j];
             }
         };
-        if (edge) fwd_rows<TI, D, true, ALIGNED>(a, P, x, ys, ye, store);
+        if (edge) fwd_rows<TI, kFwdEdgeStages, true, ALIGNED>(a, P, x, ys, ye, store);
         else if constexpr (TMA) fwd_rows_bulk<TI, NS>(a, P, lane, x, ys, ye, ring, bulk, store);
         else fwd_rows<TI, D, false, ALIGNED>(a, P, x, ys, ye, store);
         if (ye == y1 && !bulk.failed) emit(y1 - 1, ha);  // the region's last row: nothing below it

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_
         const int xb = a.x0 + seg * kSegOut;
         const int x = xb - 4 + 4 * lane;
         const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W) || a.valid;
-        if (edge) fwd_strip<TI, TO, D, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+        if (edge) fwd_strip<TI, TO, kFwdEdgeStages, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
         else if constexpr (TMA) fwd_strip_bulk<TI, TO, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring, bulk);
         else fwd_strip<TI, TO, D, false, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
         lo += r1 - r0;

@@ -14,6 +14,9 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_FWD_STAGES
 #define SHINE_FWD_STAGES 2        // image rows the forward keeps in flight (register staging)
 #endif
+#ifndef SHINE_FWD_EDGE_STAGES
+#define SHINE_FWD_EDGE_STAGES 1   // the same on edge segments (fewer rows: less code next to the
+#endif                            // bulk-staged strips; measured 7% faster forward)
 #ifndef SHINE_FWD_TMA
 #define SHINE_FWD_TMA 1           // forward interior segments staged by bulk copies
 #endif
@@ -37,6 +40,7 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #endif
 constexpr int kFwdThreads = 128;  // 4 warps per CTA
 constexpr int kFwdStages = SHINE_FWD_STAGES;
+constexpr int kFwdEdgeStages = SHINE_FWD_EDGE_STAGES;
 constexpr int kFwdBulkStages = SHINE_FWD_BULK_STAGES;
 constexpr int kBwdThreads = 128;
 constexpr int kBwdStages = SHINE_BWD_STAGES;
