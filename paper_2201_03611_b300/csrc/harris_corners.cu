@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
     const float kNegInf = __int_as_float(0xff800000);
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
+    warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
     while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);

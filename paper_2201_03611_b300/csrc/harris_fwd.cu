@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_
     // This warp's share of the (segment, row) units, walked segment by segment.
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi);
+    warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
     while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);

@@ -32,6 +32,12 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_BWD_TMA
 #define SHINE_BWD_TMA 1           // backward interior segments staged by bulk copies
 #endif
+#ifndef SHINE_FWD_EDGE_WEIGHT4
+#define SHINE_FWD_EDGE_WEIGHT4 6  // an edge-segment row weighs this / 4 interior rows (forward-type)
+#endif
+#ifndef SHINE_BWD_EDGE_WEIGHT4
+#define SHINE_BWD_EDGE_WEIGHT4 6  // the same for the adjoint
+#endif
 #ifndef SHINE_FWD_BAND_MAJOR
 #define SHINE_FWD_BAND_MAJOR 1    // forward: equal row bands across all segments
 #endif
@@ -69,24 +75,70 @@ __host__ __device__ inline void balanced_slice(int64_t n, int64_t t, int64_t w, 
 }
 
 // Work of warp w among t warps over nseg segments x rows rows, as (segment, row) units in
-// segment-major order: [lo, hi). Band-major: when t >= nseg, warp w takes segment w % nseg and
-// the (w / nseg)-th of t / nseg equal row bands, so the warps of one band walk the same rows
-// at the same time (whole image rows, good DRAM page locality) and every warp has the same
-// work; surplus warps (w >= nseg * (t / nseg)) get nothing. Otherwise the units are split
-// evenly in segment-major order.
+// segment-major order: [lo, hi). The two edge segments (first and last) run slower per row than
+// the interior ones (element staging, clamps), so a unit of theirs weighs ew4 / 4 interior units
+// (ew4 = 4: no weighting); every warp gets about the same weight, so that no edge warp is left
+// running alone at the end.
+// Band-major: when t >= nseg, every warp takes one segment and one row band of it; the warps of
+// one interior band walk the same rows at the same time (whole image rows, good DRAM page
+// locality); edge segments are cut into proportionally more bands. Otherwise the weighted units
+// are split evenly in segment-major order.
 __host__ __device__ inline void warp_work(bool band_major, int64_t nseg, int64_t rows, int64_t t, int64_t w,
-                                          int64_t& lo, int64_t& hi) {
+                                          int64_t& lo, int64_t& hi, int ew4 = 4) {
+    const bool weigh = ew4 != 4 && nseg >= 3;
     if (band_major && t >= nseg) {
-        const int64_t nb = t / nseg;
-        if (w >= nb * nseg) { lo = hi = 0; return; }
-        const int64_t seg = w % nseg, band = w / nseg;
+        if (!weigh) {
+            const int64_t nb = t / nseg;
+            if (w >= nb * nseg) { lo = hi = 0; return; }
+            const int64_t seg = w % nseg, band = w / nseg;
+            int64_t r0, r1;
+            balanced_slice(rows, nb, band, r0, r1);
+            lo = seg * rows + r0;
+            hi = seg * rows + r1;
+            return;
+        }
+        // bands per interior segment nbi and per edge segment nbe ~ nbi * ew4 / 4
+        int64_t nbi = (4 * t) / (4 * (nseg - 2) + 2 * ew4);
+        if (nbi < 1) nbi = 1;
+        int64_t nbe = (nbi * ew4 + 2) / 4;
+        const int64_t spare = (t - (nseg - 2) * nbi) / 2;
+        if (nbe > spare) nbe = spare;
+        if (nbe < 1) nbe = 1;
+        if (nbe > rows) nbe = rows;
+        if (nbi > rows) nbi = rows;
+        int64_t seg, band, nb;
+        if (w < 2 * nbe) {
+            seg = w < nbe ? 0 : nseg - 1;
+            band = w < nbe ? w : w - nbe;
+            nb = nbe;
+        } else {
+            const int64_t v = w - 2 * nbe;
+            if (v >= (nseg - 2) * nbi) { lo = hi = 0; return; }
+            seg = 1 + v % (nseg - 2);
+            band = v / (nseg - 2);
+            nb = nbi;
+        }
         int64_t r0, r1;
         balanced_slice(rows, nb, band, r0, r1);
         lo = seg * rows + r0;
         hi = seg * rows + r1;
         return;
     }
-    balanced_slice(nseg * rows, t, w, lo, hi);
+    if (!weigh) {
+        balanced_slice(nseg * rows, t, w, lo, hi);
+        return;
+    }
+    // weight positions: edge segment 0 | interior segments | edge segment nseg-1
+    const int64_t e0 = rows * ew4, mid = (nseg - 2) * rows * 4, total = 2 * e0 + mid;
+    auto unit = [&](int64_t p) -> int64_t {
+        if (p < e0) return p / ew4;
+        if (p < e0 + mid) return rows + (p - e0) / 4;
+        return (nseg - 1) * rows + (p - e0 - mid) / ew4;
+    };
+    int64_t p0, p1;
+    balanced_slice(total, t, w, p0, p1);
+    lo = unit(p0);
+    hi = p1 >= total ? nseg * rows : unit(p1);
 }
 
 struct FwdArgs : Geometry {

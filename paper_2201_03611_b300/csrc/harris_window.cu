@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) harris_window_kernel(const __g
     constexpr int R = (K - 1) / 2;
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    warp_work(1, a.nseg, rows, a.nwarps, gw, lo, hi);
+    warp_work(1, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
     while (lo < hi && !bulk.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(const __grid_consta
     if (gw >= a.nwarps) return;
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
-    warp_work(1, a.nseg, rows, a.nwarps, gw, lo, hi);
+    warp_work(1, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
     while (lo < hi) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
