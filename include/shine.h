@@ -339,6 +339,16 @@ SHINE_API shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda
 SHINE_API shine_status shine_wait_status(int* failed, int clear);
 
 /*
+ * Host-side view of the work partition the kernels use (no counterpart in the paper; for tests
+ * and tuning): the (segment, row) units [*lo, *hi), in segment-major order, that warp w of t
+ * takes over nseg column segments of rows rows; band_major != 0 selects the band-major layout
+ * (one segment and one row band per warp when t >= nseg), edge_weight4 / 4 is the weight of an
+ * edge-segment row against an interior row (4: unweighted). No GPU is touched.
+ */
+SHINE_API shine_status shine_partition(int64_t nseg, int64_t rows, int64_t t, int64_t w, int32_t band_major,
+                                       int32_t edge_weight4, int64_t* lo, int64_t* hi);
+
+/*
  * Self-test of the bounded-wait path (no counterpart in the paper): launches one warp that
  * waits, with at most max_spins polls (1 .. 2^22), on a shared-memory barrier that nothing
  * completes, and writes 1 to *result (a device int) when the wait gave up -- as it must -- and

@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
         "shine_pipeline_host": (st, [p, p, p, p, i64, i64, f, f, p, p, p, p, p, p, p, p, p, sz, i32, p]),
         "shine_mv": (st, [p, i64, i64, i64, f, p, p, p]),
         "shine_wait_status": (st, [ctypes.POINTER(f), f]),
+        "shine_partition": (st, [i64, i64, i64, i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "shine_selftest_bounded_wait": (st, [i32, p, p]),
         "shine_iterate_sum": (st, [p, i64, i32, i32, p, p]),
         "shine_iterate_reduce": (st, [p, i64, i32, i32, f, p, p]),

@@ -122,6 +122,14 @@ const char* shine_status_string(shine_status s) {
 
 int shine_last_cuda_error(void) { return g_last_cuda_error; }
 
+shine_status shine_partition(int64_t nseg, int64_t rows, int64_t t, int64_t w, int32_t band_major,
+                             int32_t edge_weight4, int64_t* lo, int64_t* hi) {
+    if (!lo || !hi || nseg < 1 || rows < 1 || t < 1 || w < 0 || w >= t || edge_weight4 < 1 || edge_weight4 > 64)
+        return SHINE_ERR_INVALID_ARG;
+    warp_work(band_major != 0, nseg, rows, t, w, *lo, *hi, edge_weight4);
+    return SHINE_OK;
+}
+
 shine_status shine_wait_status(int* failed, int clear) {
     if (!failed) return SHINE_ERR_INVALID_ARG;
     unsigned int v = 0;
