@@ -11,6 +11,8 @@
 // Along the row the completed vertical sums are widened by r columns from the neighbouring lanes
 // (lanes 0 and 31 hold valid Sobel rows up to 3 columns beyond the segment), clamped at the image
 // edge, and weighted with gh. Window weights are host values passed in the kernel parameters.
+// The xx and yy planes travel as one packed float32 pair through both window passes (each half
+// rounds as the scalar operation would), the xy plane alone.
 #include <algorithm>
 
 #include "harris_fwd_strip.cuh"
@@ -61,9 +63,9 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
     const int H = a.H, W = a.W;
     const int s_first = y0 - R > 0 ? y0 - R : 0;  // first Sobel row used
     auto take_gray = [&](float g6[6]) { src.take(g6); };
-    float gv[K], gh[K];  // window weights held in registers for the multiply-add chains
+    float2 gv[K], gh[K];  // window weights, duplicated into both halves of a packed pair
 #pragma unroll
-    for (int i = 0; i < K; ++i) { gv[i] = wa.gv[i]; gh[i] = wa.gh[i]; }
+    for (int i = 0; i < K; ++i) { gv[i] = dup2(wa.gv[i]); gh[i] = dup2(wa.gh[i]); }
     StripRun st;
 #pragma unroll
     for (int j = 0; j < 4; ++j) st.P1[j] = st.P2[j] = make_float2(0.0f, 0.0f);
@@ -75,13 +77,13 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
     }
     int cur_s = s_first;
 
-    float vacc[NA][3][4];  // partial vertical window sums per plane (xx, xy, yy)
+    // Partial vertical window sums: the xx and yy planes packed in one pair, xy alone.
+    float2 vacc[NA][4];
+    float vaxy[NA][4];
 #pragma unroll
     for (int i = 0; i < NA; ++i)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) vacc[i][c][j] = 0.0f;
+        for (int j = 0; j < 4; ++j) { vacc[i][j] = make_float2(0.0f, 0.0f); vaxy[i][j] = 0.0f; }
     const bool producer = lane >= 1 && lane <= 30;
     TO* out = static_cast<TO*>(a.out);
 
@@ -93,58 +95,71 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
             push_gray(P, g, st);
             ++cur_s;
         }
-        float prod[3][4];
+        // window position q = p - (y0 - R): output row p - R completes once q >= K-1
+        float2 done[4];
+        float dxy[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            prod[0][j] = __fmul_rn(st.S[j].x, st.S[j].x);
-            prod[1][j] = __fmul_rn(st.S[j].x, st.S[j].y);
-            prod[2][j] = __fmul_rn(st.S[j].y, st.S[j].y);
-        }
-        // window position q = p - (y0 - R): output row p - R completes once q >= K-1
-        float done[3][4];
+            const float2 p2 = __fmul2_rn(st.S[j], st.S[j]);  // (Sx^2, Sy^2)
+            const float pxy = __fmul_rn(st.S[j].x, st.S[j].y);
+            done[j] = __ffma2_rn(gv[K - 1], p2, vacc[0][j]);
+            dxy[j] = fmaf(gv[K - 1].x, pxy, vaxy[0][j]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                done[c][j] = fmaf(gv[K - 1], prod[c][j], vacc[0][c][j]);
-#pragma unroll
-                for (int i = 0; i + 1 < NA; ++i) vacc[i][c][j] = fmaf(gv[K - 2 - i], prod[c][j], vacc[i + 1][c][j]);
-                vacc[NA - 1][c][j] = fmaf(gv[0], prod[c][j], 0.0f);
+            for (int i = 0; i + 1 < NA; ++i) {
+                vacc[i][j] = __ffma2_rn(gv[K - 2 - i], p2, vacc[i + 1][j]);
+                vaxy[i][j] = fmaf(gv[K - 2 - i].x, pxy, vaxy[i + 1][j]);
             }
+            vacc[NA - 1][j] = __ffma2_rn(gv[0], p2, make_float2(0.0f, 0.0f));
+            vaxy[NA - 1][j] = fmaf(gv[0].x, pxy, 0.0f);
+        }
         if (p - (y0 - R) < K - 1) continue;
         const int y = p - R;
         float S3[3][4];
+        {
+            float ex[4 + 2 * R], ey[4 + 2 * R], exy[4 + 2 * R];
+            float cx[4], cy[4];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float e[4 + 2 * R];
-            widen<R>(done[c], e);
-            if constexpr (EDGE) clamp_widened<4 + 2 * R>(e, x - R, W);
+            for (int j = 0; j < 4; ++j) { cx[j] = done[j].x; cy[j] = done[j].y; }
+            widen<R>(cx, ex);
+            widen<R>(cy, ey);
+            widen<R>(dxy, exy);
+            if constexpr (EDGE) {
+                clamp_widened<4 + 2 * R>(ex, x - R, W);
+                clamp_widened<4 + 2 * R>(ey, x - R, W);
+                clamp_widened<4 + 2 * R>(exy, x - R, W);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float t = 0.0f;
+                float2 t = make_float2(0.0f, 0.0f);
+                float txy = 0.0f;
 #pragma unroll
-                for (int b = 0; b < K; ++b) t = fmaf(gh[b], e[j + b], t);
-                S3[c][j] = t;
+                for (int b = 0; b < K; ++b) {
+                    t = __ffma2_rn(gh[b], make_float2(ex[j + b], ey[j + b]), t);
+                    txy = fmaf(gh[b].x, exy[j + b], txy);
+                }
+                S3[0][j] = t.x;
+                S3[1][j] = txy;
+                S3[2][j] = t.y;
             }
         }
-        if (producer) {
-            float Rv[4];
+        float Rv[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) Rv[j] = response(S3[0][j], S3[1][j], S3[2][j], P.kappa);
-            TO* orow = out + (int64_t)y * a.out_pitch;
-            if (!EDGE && a.out_vec) {
-                store4(orow + x, Rv);
-            } else {
+        for (int j = 0; j < 4; ++j) Rv[j] = response(S3[0][j], S3[1][j], S3[2][j], P.kappa);
+        TO* orow = out + (int64_t)y * a.out_pitch;
+        if (!EDGE && a.out_vec) {
+            if (producer) store4(orow + x, Rv);
+        } else if (producer) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (x + j >= 0 && x + j < W) orow[x + j] = Conv<TO>::st(Rv[j]);
-            }
+            for (int j = 0; j < 4; ++j)
+                if (x + j >= 0 && x + j < W) orow[x + j] = Conv<TO>::st(Rv[j]);
         }
     }
 }
 
+// K <= 5 fits 168 registers without spilling, which lets 12 warps share an SM instead of 8
+// (measured: K = 3 runs 1.5x, K = 5 1.1x faster than at 8 warps); K = 7 would spill there.
 template <typename TI, typename TO, int K, bool ALIGNED, bool TMA>
-__global__ void __launch_bounds__(kFwdThreads, 2) harris_window_kernel(const __grid_constant__ WindowArgs wa) {
+__global__ void __launch_bounds__(kFwdThreads, K <= 5 ? 3 : 2) harris_window_kernel(const __grid_constant__ WindowArgs wa) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const FwdArgs& a = wa.f;
     constexpr int NS = kFwdBulkStages;
