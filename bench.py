@@ -324,6 +324,7 @@ def run_ours(args, world, rank, local) -> dict | None:
         extras["iterate"] = iterate_extra(S, device, reps=50)
         extras["stencil"] = stencil_extra(S, device, size, reps=max(10, K // 20))
         extras["gaussian_window_harris"] = window_extra(S, device, size, reps=max(10, K // 20))
+        extras["iterate_stencil"] = iterate_stencil_extra(S, device, size, reps=max(10, K // 20))
         extras["corners"] = corners_extra(S, device, size, reps=max(10, K // 10))
         line["extras"] = extras
     return line
@@ -504,6 +505,32 @@ def stencil_extra(S, device, size: int, reps: int) -> dict:
     return out
 
 
+def iterate_stencil_extra(S, device, size: int, reps: int) -> dict:
+    """iterate with a size-preserving body: k rounds of the clamp-padded 3x3 blur on a size x size
+    float32 array, double-buffered in shared memory per tile (8 B/px of HBM traffic whatever k;
+    18 k flops/px)."""
+    out = {}
+    props = torch.cuda.get_device_properties(device)
+    fp32_peak = props.multi_processor_count * 128 * 2 * _max_sm_clock_ghz() / 1e3
+    px = size * size
+    x, W = wl.iterate_stencil_inputs(size, size, seed=0)
+    xd = x.to(device)
+    y = torch.empty(size, size, device=device)
+    stream = torch.cuda.current_stream(device)
+    for k in (1, 4, 8):
+        fn = lambda: S.iterate_stencil(xd, W, k, out=y)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = _time_ms(fn, reps, stream)
+        tf = 18 * k * px / (t * 1e-3) / 1e12
+        out[f"k{k}"] = {"ms": t, "gpix_s": px / (t * 1e-3) / 1e9,
+                        "frac_of_measured_hbm": 8 * px / (t * 1e-3) / 1e9 / _peaks()[0],
+                        "tflop_s": tf, "frac_of_fp32_peak": tf / fp32_peak}
+    del xd
+    return out
+
+
 def _max_sm_clock_ghz() -> float:
     try:
         import subprocess
@@ -651,6 +678,7 @@ EXTRAS = {
     "iterate": lambda S, d, n, r: iterate_extra(S, d, r, m=n * n // 1024, n=4, k=5),
     "stencil": lambda S, d, n, r: stencil_extra(S, d, n, r),
     "gaussian_window_harris": lambda S, d, n, r: window_extra(S, d, n, r),
+    "iterate_stencil": lambda S, d, n, r: iterate_stencil_extra(S, d, n, r),
 }
 
 

@@ -310,6 +310,26 @@ SHINE_API shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t 
                                             float* out, void* stream);
 
 /*
+ * iterate with a size-preserving body (Sec. 6, n = 1): k rounds of the clamp-padded 3x3 stencil
+ *   x_{i+1} = map(map(nbh => reduce(+, 0)(map(*)(zip(join nbh, join W)))))
+ *             (slide2D(3, 1)(pad_clamp2D(1)(x_i))),   x_0 = in,  out = x_k
+ * (an iterated blur when the weights are a smoothing kernel). Clamp padding applies before every
+ * round; W acts as a correlation, W[a][b] on x_i[y + a - 1][x + b - 1] (clamped).
+ *   in  [H][in_pitch] float32 (device; row y at in + y * in_pitch), read only
+ *   out [H][out_pitch] float32 (device, overwritten; must not overlap in)
+ *   weights [9] float32, HOST memory, row-major, copied at the call
+ * The double buffer lives in shared memory per 64 x 128 output tile (temporal blocking): round 0
+ * reads in straight from global memory, the rounds between ping-pong in shared memory, round k-1
+ * writes out. Each output is a chain of float32 fused multiply-adds per round (taps in row-major
+ * order from zero). Limits: 1 <= k <= 9; 1 <= H, W <= 2^30; pitches >= W. Errors: NULL pointers,
+ * bad sizes or overlapping in/out -> SHINE_ERR_INVALID_ARG; in/out not 4-byte aligned ->
+ * SHINE_ERR_ALIGNMENT. Asynchronous on `stream`; no allocation.
+ */
+SHINE_API shine_status shine_iterate_stencil(const float* in, int64_t H, int64_t W, int64_t in_pitch,
+                                             const float* weights, int32_t k, float* out, int64_t out_pitch,
+                                             void* stream);
+
+/*
  * Matrix-vector multiply, the paper's running example (Sec. 4, MV):
  *   y[i] = reduce(+, 0)(map(*)(zip(A[i], x)))  =  sum_j A[i][j] * x[j]
  *   A      [M][lda] elements of type dt, row-major, lda >= max(N, 1) (device)

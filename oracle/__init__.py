@@ -13,4 +13,9 @@ Python binding never do, and this package never imports them: the two share no c
 * ``mv``        -- the paper's running example (matrix-vector multiply) in both its high-level
                    and its optimised pattern form, and a row-sampled form for large matrices.
 * ``corners``   -- threshold + 3x3 non-maximum suppression of R (the corner step after A5).
+* ``stencil``   -- the generalised slide2D(K) + reduce stage (K x K and separable weights).
+* ``harris_window`` -- the Harris pipeline with a separable K-tap window at A4.
+* ``iterate_sum`` -- iterate with a shrinking body split(n) >> map(reduce(op, identity)).
+* ``iterate_stencil`` -- iterate with a size-preserving body: k rounds of the clamp-padded 3x3
+                   stencil.
 """

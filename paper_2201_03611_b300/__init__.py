@@ -11,5 +11,5 @@ fallback. Build it with ``python -m paper_2201_03611_b300.build``.
 """
 from ._lib import LIB_PATH, ShineError, lib  # noqa: F401
 from .batched import BatchedPlan  # noqa: F401
-from .ops import (HarrisFn, bwd_workspace_bytes, corners, harris, harris_window, iterate_sum, mv,  # noqa: F401
-                  output_shape, pipeline_bwd, pipeline_fwd, pipeline_fwd_bwd, stencil2d)
+from .ops import (HarrisFn, bwd_workspace_bytes, corners, harris, harris_window, iterate_stencil,  # noqa: F401
+                  iterate_sum, mv, output_shape, pipeline_bwd, pipeline_fwd, pipeline_fwd_bwd, stencil2d)

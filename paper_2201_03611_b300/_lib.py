@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         "shine_selftest_bounded_wait": (st, [i32, p, p]),
         "shine_iterate_sum": (st, [p, i64, i32, i32, p, p]),
         "shine_iterate_reduce": (st, [p, i64, i32, i32, f, p, p]),
+        "shine_iterate_stencil": (st, [p, i64, i64, i64, p, i32, p, i64, p]),
         "shine_stencil2d": (st, [p, i64, i64, i64, f, f, i32, p, p, p, p, i64, f, p]),
         "shine_harris_window": (st, [p, i64, i64, i64, f, p, p, p, i32, p, p, p, i64, f, p]),
         "shine_corners": (st, [p, i64, i64, i64, f, f, p, p, p, ctypes.c_float, p, i64, p, i64, f, p]),

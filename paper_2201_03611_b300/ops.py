@@ -254,6 +254,28 @@ def iterate_sum(x: torch.Tensor, n: int, k: int, out=None, op: str = "sum") -> t
     return out
 
 
+def iterate_stencil(x: torch.Tensor, weights, k: int, out=None) -> torch.Tensor:
+    """k rounds of the clamp-padded 3x3 stencil (iterate with a size-preserving body,
+    shine_iterate_stencil) of an (H, W) float32 CUDA array with column stride 1; weights: 3 x 3
+    host values (CPU tensor or nested sequence), applied as a correlation."""
+    if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2 or (x.shape[1] > 1 and x.stride(1) != 1):
+        raise ValueError("x must be a 2-D float32 CUDA tensor with column stride 1")
+    wt = torch.as_tensor(weights, dtype=torch.float32).cpu().contiguous()
+    if wt.shape != (3, 3):
+        raise ValueError("weights must be 3 x 3")
+    h, w = x.shape
+    if out is None:
+        out = torch.empty(h, w, device=x.device, dtype=torch.float32)
+    _check_map(out, (h, w), "out")
+    if out.dtype != torch.float32:
+        raise ValueError("out must be float32")
+    L.check(L.lib().shine_iterate_stencil(_ptr(x), h, w, _row_pitch(x) if h > 1 else max(w, 1),
+                                          ctypes.c_void_p(wt.data_ptr()), k, _ptr(out),
+                                          _row_pitch(out) if h > 1 else max(w, 1), _stream(x.device)),
+            "shine_iterate_stencil")
+    return out
+
+
 def stencil2d(x: torch.Tensor, weights=None, wv=None, wh=None, border: str = "clamp", out=None,
               out_dtype=None) -> torch.Tensor:
     """One slide2D(K, 1) + reduce stage (shine_stencil2d) of an (H, W) CUDA array (float32 or

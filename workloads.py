@@ -156,6 +156,20 @@ def iterate_inputs(m: int, n: int, k: int, seed: int) -> torch.Tensor:
     return torch.rand(n ** k * m, generator=g) * 2.0 - 1.0
 
 
+def iterate_stencil_inputs(h: int, w: int, seed: int, blur: bool = True) -> tuple[torch.Tensor, torch.Tensor]:
+    """Iterated-stencil workload: x ~ U(0, 1) of shape (h, w), then 3 x 3 weights from one
+    generator in that order: a blur (U(0, 1) weights scaled to sum 1, so repeated rounds stay
+    in range) or, with blur=False, N(0, 1) weights."""
+    g = torch.Generator().manual_seed(seed)
+    x = torch.rand(h, w, generator=g)
+    if blur:
+        W = torch.rand(3, 3, generator=g)
+        W = (W.double() / W.double().sum()).float()
+    else:
+        W = torch.randn(3, 3, generator=g)
+    return x, W
+
+
 def stencil_inputs(h: int, w: int, k: int, seed: int) -> tuple[torch.Tensor, torch.Tensor]:
     """Generalised-stencil workload: x ~ U(0, 1) of shape (h, w), then K x K weights ~ N(0, 1)
     (non-separable), float32, from one generator in that order."""
