@@ -318,10 +318,10 @@ SHINE_API shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t 
  *   in  [H][in_pitch] float32 (device; row y at in + y * in_pitch), read only
  *   out [H][out_pitch] float32 (device, overwritten; must not overlap in)
  *   weights [9] float32, HOST memory, row-major, copied at the call
- * The double buffer lives in shared memory per 64 x 128 output tile (temporal blocking): round 0
+ * The double buffer lives in shared memory per 64 x 112 output tile (temporal blocking): round 0
  * reads in straight from global memory, the rounds between ping-pong in shared memory, round k-1
  * writes out. Each output is a chain of float32 fused multiply-adds per round (taps in row-major
- * order from zero). Limits: 1 <= k <= 9; 1 <= H, W <= 2^30; pitches >= W. Errors: NULL pointers,
+ * order from zero). Limits: 1 <= k <= 8; 1 <= H, W <= 2^30; pitches >= W. Errors: NULL pointers,
  * bad sizes or overlapping in/out -> SHINE_ERR_INVALID_ARG; in/out not 4-byte aligned ->
  * SHINE_ERR_ALIGNMENT. Asynchronous on `stream`; no allocation.
  */

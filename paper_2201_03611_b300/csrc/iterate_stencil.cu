@@ -3,9 +3,9 @@
 //   body(x) = map(map(nbh => reduce(+, 0)(map(*)(zip(join nbh, join W)))))(slide2D(3, 1)(pad_clamp2D(1)(x)))
 // on an H x W float32 array, each round's output the next round's input. The two buffers of the
 // double buffer live in shared memory, one pair per tile (temporal blocking):
-//   * a CTA owns a 64 x 128 output tile and stages a 64 + 2(k-1) row by 144 column region of
+//   * a CTA owns a 64 x 112 output tile and stages a 64 + 2(k-1) row by 128 column region of
 //     every intermediate round (8 halo columns on each side, k-1 halo rows above and below: a
-//     round reaches one row and one column further, and round 0 reads its own halo);
+//     round reaches one row and one column further, and round 0 reads its own row halo);
 //   * round 0 reads the input straight from global memory (no copy into the double buffer:
 //     clamped loads, through L1), rounds 1 .. k-2 ping-pong between the two buffers, and round
 //     k-1 writes the output tile to global memory -- the swap / done structure of the paper's
@@ -13,11 +13,13 @@
 //   * per-stage clamp padding: after each intermediate round, a tile that touches the image
 //     border overwrites the positions outside the image with the round's values at the clamped
 //     positions, so the next round's stencil reads exactly pad_clamp2D(1) of that round;
-//   * each thread owns a 4-column strip of a band of rows and slides a 3-row register window
-//     down it (one new row per output row: a 16-byte shared load plus one value from each
-//     neighbouring strip), the 9 taps a fused multiply-add chain in row-major order from zero.
-// Each round's values near the tile edge go stale one row / column per round (their neighbours
-// were never staged); the halos are sized so the stale band never reaches the output tile.
+//   * each warp owns a band of rows and each lane a 4-column strip of it; the lane slides a
+//     3-row register window down its strip, four new rows loaded together (one 16-byte load per
+//     row; the neighbouring columns come from the adjacent lanes by shuffles), the 9 taps a
+//     fused multiply-add chain in row-major order from zero.
+// The outermost staged columns have no neighbour in the warp, so each round's values go stale
+// one column (and, for rounds 1.., one row) further in from the staged region's edge; the halos
+// are sized so the stale band never reaches the output tile (k <= 8).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,14 +30,14 @@
 namespace shine {
 namespace {
 
-constexpr int kItsThreads = 256;
+constexpr int kItsWarps = 8;                            // row bands per tile
+constexpr int kItsThreads = 32 * kItsWarps;
 constexpr int kItsTH = 64;                              // output rows per tile
-constexpr int kItsTW = 128;                             // output columns per tile
-constexpr int kItsHalo = 8;                             // staged columns on each side (>= k - 1)
-constexpr int kItsMaxK = kItsHalo + 1;
-constexpr int kItsCols = kItsTW + 2 * kItsHalo;         // 144 staged columns
-constexpr int kItsStrips = kItsCols / 4;                // 36 four-column strips
-constexpr int kItsBands = kItsThreads / kItsStrips;     // 7 row bands (252 threads busy)
+constexpr int kItsHalo = 8;                             // staged columns on each side (>= k)
+constexpr int kItsCols = 128;                           // staged columns: 4 per lane
+constexpr int kItsTW = kItsCols - 2 * kItsHalo;         // 112 output columns per tile
+constexpr int kItsMaxK = kItsHalo;
+constexpr unsigned kItsFull = 0xffffffffu;
 
 struct ItsArgs {
     const float* in;
@@ -51,7 +53,25 @@ struct ItsArgs {
 
 __device__ __forceinline__ int clampi_its(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
-// One output row of the strip: rows r0 (above), r1, r2 (below) hold columns 4s-1 .. 4s+4.
+__device__ __forceinline__ float4 its_lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void its_sts128(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// The lane's 4 values widened by one column from each neighbouring lane (row6: columns
+// 4 lane - 1 .. 4 lane + 4); lanes 0 and 31 repeat their own edge value (stale columns).
+__device__ __forceinline__ void its_widen(float4 q, float v[6]) {
+    v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+    v[0] = __shfl_up_sync(kItsFull, q.w, 1);
+    v[5] = __shfl_down_sync(kItsFull, q.x, 1);
+}
+
+// One output row of the strip: rows r0 (above), r1, r2 (below) hold columns 4 lane - 1 .. +4.
 __device__ __forceinline__ void its_row(const ItsArgs& a, const float r0[6], const float r1[6], const float r2[6],
                                         float o[4]) {
 #pragma unroll
@@ -67,92 +87,101 @@ __device__ __forceinline__ void its_row(const ItsArgs& a, const float r0[6], con
     }
 }
 
+// Rows [r0, r1) of one round for this lane's strip: load(r, v) delivers a widened input row,
+// emit(r, o) takes an output row. Four new rows are loaded together per iteration so that
+// every lane keeps four loads in flight.
+template <typename Load, typename Emit>
+__device__ __forceinline__ void its_band(const ItsArgs& a, int r0, int r1, Load&& load, Emit&& emit) {
+    float A[6], B[6], C[6], D[6], E[6], F[6], o[4];
+    load(r0 - 1, A);
+    load(r0, B);
+    int r = r0;
+    for (; r + 4 <= r1; r += 4) {
+        load(r + 1, C);
+        load(r + 2, D);
+        load(r + 3, E);
+        load(r + 4, F);
+        its_row(a, A, B, C, o); emit(r, o);
+        its_row(a, B, C, D, o); emit(r + 1, o);
+        its_row(a, C, D, E, o); emit(r + 2, o);
+        its_row(a, D, E, F, o); emit(r + 3, o);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { A[j] = E[j]; B[j] = F[j]; }
+    }
+    for (; r < r1; ++r) {
+        load(r + 1, C);
+        its_row(a, A, B, C, o); emit(r, o);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { A[j] = B[j]; B[j] = C[j]; }
+    }
+}
+
 __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __grid_constant__ ItsArgs a) {
     extern __shared__ __align__(16) float its_smem[];
-    const int tid = threadIdx.x;
-    const int s = tid % kItsStrips;   // strip: staged columns 4s .. 4s+3
-    const int band = tid / kItsStrips;
-    const bool busy = band < kItsBands;
+    const int lane = threadIdx.x & 31;
+    const int band = threadIdx.x >> 5;
     const int k = a.k;
     const int TH2 = kItsTH + 2 * (k - 1);  // staged rows
     const int ty0 = (int)(blockIdx.x / a.tiles_x) * kItsTH;
     const int tx0 = (int)(blockIdx.x % a.tiles_x) * kItsTW;
     const int gy0 = ty0 - (k - 1);   // global row of staged row 0
     const int gx0 = tx0 - kItsHalo;  // global column of staged column 0
+    const int gx = gx0 + 4 * lane;   // the lane's first column
     const bool border = gy0 < 0 || gx0 < 0 || gy0 + TH2 > a.H || gx0 + kItsCols > a.W;
-    float* buf[2] = {its_smem, its_smem + (size_t)TH2 * kItsCols};
+    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(its_smem);
+    const uint32_t sbuf_bytes = (uint32_t)TH2 * kItsCols * 4u;
+    const uint32_t lane_off = 16u * (uint32_t)lane;
 
     // Row r (staged coordinates) of round 0's input: global, clamped.
     auto load_global = [&](int r, float v[6]) {
-        const int gy = clampi_its(gy0 + r, a.H);
-        const float* row = a.in + (int64_t)gy * a.in_pitch;
-        const int gx = gx0 + 4 * s;
+        const float* row = a.in + (int64_t)clampi_its(gy0 + r, a.H) * a.in_pitch;
+        float4 q;
         if (a.vec_in && gx >= 0 && gx + 3 < a.W) {
-            const float4 q = __ldg(reinterpret_cast<const float4*>(row + gx));
-            v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+            q = __ldg(reinterpret_cast<const float4*>(row + gx));
         } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[1 + j] = __ldg(row + clampi_its(gx + j, a.W));
+            q.x = __ldg(row + clampi_its(gx, a.W));
+            q.y = __ldg(row + clampi_its(gx + 1, a.W));
+            q.z = __ldg(row + clampi_its(gx + 2, a.W));
+            q.w = __ldg(row + clampi_its(gx + 3, a.W));
         }
-        v[0] = __ldg(row + clampi_its(gx - 1, a.W));
-        v[5] = __ldg(row + clampi_its(gx + 4, a.W));
+        its_widen(q, v);
     };
-    // Row r of a staged buffer (the strips at the region's two ends read their own edge value
-    // for the missing neighbour column: stale positions, never used for the output).
-    auto load_shared = [&](const float* src, int r, float v[6]) {
-        const float* row = src + (size_t)r * kItsCols + 4 * s;
-        const float4 q = *reinterpret_cast<const float4*>(row);
-        v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
-        v[0] = s > 0 ? row[-1] : q.x;
-        v[5] = s < kItsStrips - 1 ? row[4] : q.w;
+    // The final round's rows go to the output tile (staged columns 8 .. 119, rows inside it).
+    const bool out_lane = lane >= kItsHalo / 4 && lane < (kItsHalo + kItsTW) / 4 && gx < a.W;
+    const bool out_vec = a.vec_out && gx + 3 < a.W;
+    auto emit_global = [&](int r, const float o[4]) {
+        const int gy = gy0 + r;
+        if (out_lane && gy < a.H) {
+            float* orow = a.out + (int64_t)gy * a.out_pitch + gx;
+            if (out_vec) {
+                *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (gx + j < a.W) orow[j] = o[j];
+            }
+        }
     };
 
     for (int i = 0; i < k; ++i) {
         const bool last = i == k - 1;
-        const float* src = i == 0 ? nullptr : buf[(i - 1) & 1];
-        float* dst = buf[i & 1];
+        const uint32_t src = sbuf0 + ((i - 1) & 1) * sbuf_bytes + lane_off;  // rounds >= 1
+        const uint32_t dst = sbuf0 + (i & 1) * sbuf_bytes + lane_off;
         const int lo = i, hi = TH2 - i;  // rows this round produces (round 0: all staged rows)
-        if (busy) {
-            const int per = (hi - lo + kItsBands - 1) / kItsBands;
-            const int r0 = lo + band * per;
-            const int r1 = min(r0 + per, hi);
-            auto load = [&](int r, float v[6]) {
-                if (i == 0) load_global(r, v);
-                else load_shared(src, r, v);
-            };
-            auto emit = [&](int r, const float o[4]) {
-                if (!last) {
-                    *reinterpret_cast<float4*>(dst + (size_t)r * kItsCols + 4 * s) = make_float4(o[0], o[1], o[2], o[3]);
-                } else {
-                    const int gy = gy0 + r, gx = gx0 + 4 * s;
-                    if (s >= kItsHalo / 4 && s < (kItsHalo + kItsTW) / 4 && gy < a.H && gx < a.W) {
-                        float* orow = a.out + (int64_t)gy * a.out_pitch;
-                        if (a.vec_out && gx + 3 < a.W) {
-                            *reinterpret_cast<float4*>(orow + gx) = make_float4(o[0], o[1], o[2], o[3]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (gx + j < a.W) orow[gx + j] = o[j];
-                        }
-                    }
-                }
-            };
-            if (r0 < r1) {
-                // sliding 3-row window; the loop rotates the three registers by name, so no
-                // row is copied
-                float A[6], B[6], C[6], o[4];
-                load(r0 - 1, A);
-                load(r0, B);
-                int r = r0;
-                for (; r + 3 <= r1; r += 3) {
-                    load(r + 1, C); its_row(a, A, B, C, o); emit(r, o);
-                    load(r + 2, A); its_row(a, B, C, A, o); emit(r + 1, o);
-                    load(r + 3, B); its_row(a, C, A, B, o); emit(r + 2, o);
-                }
-                if (r < r1) {
-                    load(r + 1, C); its_row(a, A, B, C, o); emit(r, o);
-                    if (r + 1 < r1) { load(r + 2, A); its_row(a, B, C, A, o); emit(r + 1, o); }
-                }
+        const int per = (hi - lo + kItsWarps - 1) / kItsWarps;
+        const int r0 = lo + band * per;
+        const int r1 = min(r0 + per, hi);
+        auto load_shared = [&](int r, float v[6]) { its_widen(its_lds128(src + (uint32_t)r * (kItsCols * 4)), v); };
+        auto emit_shared = [&](int r, const float o[4]) {
+            its_sts128(dst + (uint32_t)r * (kItsCols * 4), o[0], o[1], o[2], o[3]);
+        };
+        if (r0 < r1) {  // whole warp (r0, r1 depend on the band only)
+            if (i == 0) {
+                if (last) its_band(a, r0, r1, load_global, emit_global);
+                else its_band(a, r0, r1, load_global, emit_shared);
+            } else {
+                if (last) its_band(a, r0, r1, load_shared, emit_global);
+                else its_band(a, r0, r1, load_shared, emit_shared);
             }
         }
         if (last) break;
@@ -160,13 +189,14 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
         if (border) {
             // pad_clamp2D(1) of this round for the next: staged positions outside the image take
             // the round's value at the clamped position (inside the image, so not written here).
+            float* d = its_smem + (size_t)(i & 1) * TH2 * kItsCols;
             const int n = TH2 * kItsCols;
-            for (int e = tid; e < n; e += kItsThreads) {
+            for (int e = threadIdx.x; e < n; e += kItsThreads) {
                 const int r = e / kItsCols, c = e % kItsCols;
-                const int gy = gy0 + r, gx = gx0 + c;
-                if (gy < 0 || gy >= a.H || gx < 0 || gx >= a.W) {
-                    const int rr = clampi_its(gy, a.H) - gy0, cc = clampi_its(gx, a.W) - gx0;
-                    if (rr >= 0 && rr < TH2 && cc >= 0 && cc < kItsCols) dst[e] = dst[(size_t)rr * kItsCols + cc];
+                const int gy = gy0 + r, gxe = gx0 + c;
+                if (gy < 0 || gy >= a.H || gxe < 0 || gxe >= a.W) {
+                    const int rr = clampi_its(gy, a.H) - gy0, cc = clampi_its(gxe, a.W) - gx0;
+                    if (rr >= 0 && rr < TH2 && cc >= 0 && cc < kItsCols) d[e] = d[(size_t)rr * kItsCols + cc];
                 }
             }
             __syncthreads();

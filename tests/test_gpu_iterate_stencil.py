@@ -29,11 +29,11 @@ def _check(got, ref, scale, k):
     assert np.all(err <= tol), float((err / tol).max())
 
 
-# several tiles (64 x 128) with ragged edges, single rows and columns, tiles smaller than the halo
-SHAPES = [(1, 1), (1, 300), (300, 1), (5, 7), (64, 128), (65, 129), (200, 333), (131, 515)]
+# several tiles (64 x 112) with ragged edges, single rows and columns, tiles smaller than the halo
+SHAPES = [(1, 1), (1, 300), (300, 1), (5, 7), (64, 112), (65, 113), (200, 333), (131, 515)]
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 5, 9])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_iterate_stencil_matches_oracle(shine, k, shape):
     h, w = shape
@@ -63,8 +63,8 @@ def test_full_size_sampled(shine):
     x, W = wl.iterate_stencil_inputs(h, w, seed=4)
     got = shine.iterate_stencil(x.cuda(), W, k).cpu().numpy()
     rng = np.random.default_rng(0)
-    pts = [(0, 0), (0, w - 1), (h - 1, 0), (h - 1, w - 1), (1, 2), (h - 2, w - 3), (63, 127), (64, 128),
-           (65, 129), (127, 255), (128, 256)]
+    pts = [(0, 0), (0, w - 1), (h - 1, 0), (h - 1, w - 1), (1, 2), (h - 2, w - 3), (63, 111), (64, 112),
+           (65, 113), (127, 223), (128, 224), (8191, 8175), (8190, 8176)]
     pts += [(int(rng.integers(h)), c) for c in (0, 1, 3, 4, w - 5, w - 1) for _ in range(4)]
     pts += [(r, int(rng.integers(w))) for r in (0, 2, 3, 4, h - 5, h - 1) for _ in range(4)]
     pts += [tuple(int(v) for v in rng.integers(0, (h, w))) for _ in range(200)]
@@ -89,7 +89,7 @@ def test_argument_errors(shine):
     from paper_2201_03611_b300 import _lib as L
     x = torch.rand(16, 16, device="cuda")
     W = torch.rand(3, 3)
-    for bad_k in (0, 10):
+    for bad_k in (0, 9):
         with pytest.raises(L.ShineError):
             shine.iterate_stencil(x, W, bad_k)
     with pytest.raises(L.ShineError):
