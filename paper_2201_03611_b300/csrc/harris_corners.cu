@@ -9,6 +9,7 @@
 // segment) and reduced to horizontal 3-maxima; running maxima of the last rows then decide row
 // y-1 when row y arrives.
 #include <algorithm>
+#include <type_traits>
 
 #include "harris_fwd_strip.cuh"
 #include "shine_host.h"
@@ -68,8 +69,11 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
         for (int j = 0; j < 4; ++j) ha[j] = hb[j] = cen[j] = kNegInf;
 
         // Decide row y: corner where the centre exceeds the threshold and equals the maximum of
-        // its 3x3 window (that is, is >= each of its 8 neighbours).
-        auto emit = [&](int y, const float nb[4]) {
+        // its 3x3 window (that is, is >= each of its 8 neighbours). E: an edge segment (or the
+        // VALID region), where some of the lane's columns may lie outside the output region;
+        // interior segments know at compile time that all four are inside.
+        auto emit = [&](auto edge_tag, int y, const float nb[4]) {
+            constexpr bool E = decltype(edge_tag)::value;
             uint32_t bits = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -78,28 +82,29 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
             }
             if (!producer) return;
             uint8_t* mrow = c.mask + (int64_t)(y - a.oy) * c.mask_pitch;
-            if (!edge && c.mask_vec) {
+            if (!E && c.mask_vec) {
                 *reinterpret_cast<uint32_t*>(mrow + (x - a.ox)) = bits;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (cin[j]) mrow[x + j - a.ox] = (uint8_t)((bits >> (8 * j)) & 0xffu);
+                    if (!E || cin[j]) mrow[x + j - a.ox] = (uint8_t)((bits >> (8 * j)) & 0xffu);
             }
         };
-        auto store = [&](int y, const float R[4]) {
+        auto store = [&](auto edge_tag, int y, const float R[4]) {
+            constexpr bool E = decltype(edge_tag)::value;
             if (a.out != nullptr && producer && y >= y0 && y < y1) {
                 TO* orow = static_cast<TO*>(a.out) + (int64_t)(y - a.oy) * a.out_pitch;
-                if (!edge && a.out_vec) {
+                if (!E && a.out_vec) {
                     store4(orow + x, R);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if (cin[j]) orow[x + j - a.ox] = Conv<TO>::st(R[j]);
+                        if (!E || cin[j]) orow[x + j - a.ox] = Conv<TO>::st(R[j]);
                 }
             }
             float r[4], r6[6], hm[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) r[j] = cin[j] ? R[j] : kNegInf;
+            for (int j = 0; j < 4; ++j) r[j] = (!E || cin[j]) ? R[j] : kNegInf;
             make_row6(r, r6);
 #pragma unroll
             for (int j = 0; j < 4; ++j) hm[j] = fmaxf(fmaxf(r6[j], r6[j + 1]), r6[j + 2]);
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
                 float nb[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) nb[j] = fmaxf(ha[j], hm[j]);
-                emit(y - 1, nb);
+                emit(edge_tag, y - 1, nb);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -116,10 +121,21 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_M
                 cen[j] = r[j];
             }
         };
-        if (edge) fwd_rows<TI, kFwdEdgeStages, true, ALIGNED>(a, P, x, ys, ye, store);
-        else if constexpr (TMA) fwd_rows_bulk<TI, NS>(a, P, lane, x, ys, ye, ring, bulk, store);
-        else fwd_rows<TI, D, false, ALIGNED>(a, P, x, ys, ye, store);
-        if (ye == y1 && !bulk.failed) emit(y1 - 1, ha);  // the region's last row: nothing below it
+        const std::integral_constant<bool, true> on_edge{};
+        const std::integral_constant<bool, false> inside{};
+        if (edge) {
+            fwd_rows<TI, kFwdEdgeStages, true, ALIGNED>(a, P, x, ys, ye,
+                                                        [&](int y, const float R[4]) { store(on_edge, y, R); });
+        } else if constexpr (TMA) {
+            fwd_rows_bulk<TI, NS>(a, P, lane, x, ys, ye, ring, bulk,
+                                  [&](int y, const float R[4]) { store(inside, y, R); });
+        } else {
+            fwd_rows<TI, D, false, ALIGNED>(a, P, x, ys, ye, [&](int y, const float R[4]) { store(inside, y, R); });
+        }
+        if (ye == y1 && !bulk.failed) {  // the region's last row: nothing below it
+            if (edge) emit(on_edge, y1 - 1, ha);
+            else emit(inside, y1 - 1, ha);
+        }
         lo += r1 - r0;
     }
     if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
