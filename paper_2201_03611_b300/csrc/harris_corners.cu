@@ -18,8 +18,11 @@ namespace shine {
 
 namespace {
 
+// float32 register cap: the bulk-staged variant fits 128 registers (16 warps per SM) without
+// spilling; the others keep 168 (12 warps), where they do not spill either.
 template <typename TI, typename TO, int D, bool ALIGNED, bool TMA>
-__global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? 3 : SHINE_FWD_MIN_BLOCKS) harris_corners_kernel(CornerArgs c) {
+__global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? (TMA ? 4 : 3) : SHINE_FWD_MIN_BLOCKS)
+    harris_corners_kernel(CornerArgs c) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const FwdArgs& a = c.f;
     constexpr int NS = kFwdBulkStages;
