@@ -163,6 +163,19 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
         }
     };
 
+    // Tiles whose staged region, plus the row above and below it that round 0 reads, lies
+    // inside the image (with 16-byte aligned rows) take loads and stores with no clamp or bound
+    // test: a per-lane test there is turned into predicated code that issues both paths.
+    const bool fast = gy0 >= 1 && gy0 + TH2 + 1 <= a.H && gx0 >= 0 && gx0 + kItsCols <= a.W && a.vec_in && a.vec_out;
+    const bool store_lane = lane >= kItsHalo / 4 && lane < (kItsHalo + kItsTW) / 4;
+    auto load_global_fast = [&](int r, float v[6]) {
+        its_widen(__ldg(reinterpret_cast<const float4*>(a.in + (int64_t)(gy0 + r) * a.in_pitch + gx)), v);
+    };
+    auto emit_global_fast = [&](int r, const float o[4]) {
+        if (store_lane)
+            *reinterpret_cast<float4*>(a.out + (int64_t)(gy0 + r) * a.out_pitch + gx) = make_float4(o[0], o[1], o[2], o[3]);
+    };
+
     for (int i = 0; i < k; ++i) {
         const bool last = i == k - 1;
         const uint32_t src = sbuf0 + ((i - 1) & 1) * sbuf_bytes + lane_off;  // rounds >= 1
@@ -177,11 +190,20 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
         };
         if (r0 < r1) {  // whole warp (r0, r1 depend on the band only)
             if (i == 0) {
-                if (last) its_band(a, r0, r1, load_global, emit_global);
-                else its_band(a, r0, r1, load_global, emit_shared);
+                if (fast) {
+                    if (last) its_band(a, r0, r1, load_global_fast, emit_global_fast);
+                    else its_band(a, r0, r1, load_global_fast, emit_shared);
+                } else {
+                    if (last) its_band(a, r0, r1, load_global, emit_global);
+                    else its_band(a, r0, r1, load_global, emit_shared);
+                }
             } else {
-                if (last) its_band(a, r0, r1, load_shared, emit_global);
-                else its_band(a, r0, r1, load_shared, emit_shared);
+                if (last) {
+                    if (fast) its_band(a, r0, r1, load_shared, emit_global_fast);
+                    else its_band(a, r0, r1, load_shared, emit_global);
+                } else {
+                    its_band(a, r0, r1, load_shared, emit_shared);
+                }
             }
         }
         if (last) break;
