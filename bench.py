@@ -711,6 +711,7 @@ EXTRAS = {
     "iterate_stencil": lambda S, d, n, r: iterate_stencil_extra(S, d, n, r),
     "small_configs": lambda S, d, n, r: small_configs_extra(S, d, max(r, 10)),
     "precision": lambda S, d, n, r: precision_extra(S, d, n, r),
+    "batched": lambda S, d, n, r: batched_extra(S, d, n=512, reps=max(r, 10)),
 }
 
 

@@ -328,7 +328,10 @@ shine_status shine_plan_create(const int64_t* HW, int32_t n, shine_dtype dt, shi
             const int y0 = g.ylo + band * br, y1 = std::min(y0 + br, g.yhi);
             for (int seg = 0; seg < g.nseg; ++seg) {
                 const int id = (int)items.size();
-                items.push_back({i, seg, band, id, (y1 - y0) + halo});
+                // edge segments (clamps, element-wise staging) run about 1.5x slower per row
+                const int xb = g.x0 + seg * kSegOut;
+                const bool edge = xb - 4 < 0 || xb + kSegOut + 4 > g.W;
+                items.push_back({i, seg, band, id, ((y1 - y0) + halo) * (edge ? 3 : 2)});
             }
         }
         if (items.size() > (size_t)(1 << 30)) { delete p; return SHINE_ERR_INVALID_ARG; }
