@@ -13,9 +13,9 @@
 //   * per-stage clamp padding: after each intermediate round, a tile that touches the image
 //     border overwrites the positions outside the image with the round's values at the clamped
 //     positions, so the next round's stencil reads exactly pad_clamp2D(1) of that round;
-//   * each warp owns a band of rows and each lane a 4-column strip of it; the lane slides a
-//     3-row register window down its strip, four new rows loaded together (one 16-byte load per
-//     row; the neighbouring columns come from the adjacent lanes by shuffles), the 9 taps a
+//   * each warp owns a band of rows and each lane a 4-column strip of it (SHINE_ITS_PX); the
+//     lane slides a 3-row register window down its strip, four new rows loaded together (16-byte
+//     loads; the neighbouring columns come from the adjacent lanes by shuffles), the 9 taps a
 //     fused multiply-add chain in row-major order from zero.
 // The outermost staged columns have no neighbour in the warp, so each round's values go stale
 // one column (and, for rounds 1.., one row) further in from the staged region's edge; the halos
@@ -30,12 +30,23 @@
 namespace shine {
 namespace {
 
+// Tile shape knobs (measured on 8192^2, k = 4: 4 columns per lane and 64 rows 0.23 ms; 4 and 32
+// rows 0.28 ms; 8 columns and 32 rows 0.29 ms; 8 and 64 rows, one CTA per SM, 0.36 ms).
+#ifndef SHINE_ITS_PX
+#define SHINE_ITS_PX 4
+#endif
+#ifndef SHINE_ITS_TH
+#define SHINE_ITS_TH 64
+#endif
 constexpr int kItsWarps = 8;                            // row bands per tile
 constexpr int kItsThreads = 32 * kItsWarps;
-constexpr int kItsTH = 64;                              // output rows per tile
+constexpr int kItsPx = SHINE_ITS_PX;                    // columns per lane (a multiple of 4)
+constexpr int kItsQ = kItsPx / 4;                       // 16-byte chunks per lane and row
+constexpr int kItsTH = SHINE_ITS_TH;                    // output rows per tile
 constexpr int kItsHalo = 8;                             // staged columns on each side (>= k)
-constexpr int kItsCols = 128;                           // staged columns: 4 per lane
-constexpr int kItsTW = kItsCols - 2 * kItsHalo;         // 112 output columns per tile
+constexpr int kItsCols = 32 * kItsPx;                   // staged columns
+constexpr int kItsTW = kItsCols - 2 * kItsHalo;         // output columns per tile
+static_assert(kItsPx % 4 == 0 && kItsHalo % kItsPx == 0, "whole 16-byte chunks per lane; halo of whole lanes");
 constexpr int kItsMaxK = kItsHalo;
 constexpr unsigned kItsFull = 0xffffffffu;
 
@@ -63,19 +74,22 @@ __device__ __forceinline__ void its_sts128(uint32_t addr, float a, float b, floa
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-// The lane's 4 values widened by one column from each neighbouring lane (row6: columns
-// 4 lane - 1 .. 4 lane + 4); lanes 0 and 31 repeat their own edge value (stale columns).
-__device__ __forceinline__ void its_widen(float4 q, float v[6]) {
-    v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
-    v[0] = __shfl_up_sync(kItsFull, q.w, 1);
-    v[5] = __shfl_down_sync(kItsFull, q.x, 1);
+// The lane's kItsPx values widened by one column from each neighbouring lane (columns
+// P lane - 1 .. P lane + P); lanes 0 and 31 repeat their own edge value (stale columns).
+__device__ __forceinline__ void its_widen(const float4 q[kItsQ], float v[kItsPx + 2]) {
+#pragma unroll
+    for (int u = 0; u < kItsQ; ++u) {
+        v[1 + 4 * u] = q[u].x; v[2 + 4 * u] = q[u].y; v[3 + 4 * u] = q[u].z; v[4 + 4 * u] = q[u].w;
+    }
+    v[0] = __shfl_up_sync(kItsFull, q[kItsQ - 1].w, 1);
+    v[kItsPx + 1] = __shfl_down_sync(kItsFull, q[0].x, 1);
 }
 
-// One output row of the strip: rows r0 (above), r1, r2 (below) hold columns 4 lane - 1 .. +4.
-__device__ __forceinline__ void its_row(const ItsArgs& a, const float r0[6], const float r1[6], const float r2[6],
-                                        float o[4]) {
+// One output row of the strip: rows r0 (above), r1, r2 (below) hold the widened columns.
+__device__ __forceinline__ void its_row(const ItsArgs& a, const float r0[kItsPx + 2], const float r1[kItsPx + 2],
+                                        const float r2[kItsPx + 2], float o[kItsPx]) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kItsPx; ++j) {
         float t = 0.0f;
 #pragma unroll
         for (int b = 0; b < 3; ++b) t = fmaf(a.w[b], r0[j + b], t);
@@ -92,7 +106,7 @@ __device__ __forceinline__ void its_row(const ItsArgs& a, const float r0[6], con
 // every lane keeps four loads in flight.
 template <typename Load, typename Emit>
 __device__ __forceinline__ void its_band(const ItsArgs& a, int r0, int r1, Load&& load, Emit&& emit) {
-    float A[6], B[6], C[6], D[6], E[6], F[6], o[4];
+    float A[kItsPx + 2], B[kItsPx + 2], C[kItsPx + 2], D[kItsPx + 2], E[kItsPx + 2], F[kItsPx + 2], o[kItsPx];
     load(r0 - 1, A);
     load(r0, B);
     int r = r0;
@@ -106,13 +120,13 @@ __device__ __forceinline__ void its_band(const ItsArgs& a, int r0, int r1, Load&
         its_row(a, C, D, E, o); emit(r + 2, o);
         its_row(a, D, E, F, o); emit(r + 3, o);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) { A[j] = E[j]; B[j] = F[j]; }
+        for (int j = 0; j < kItsPx + 2; ++j) { A[j] = E[j]; B[j] = F[j]; }
     }
     for (; r < r1; ++r) {
         load(r + 1, C);
         its_row(a, A, B, C, o); emit(r, o);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) { A[j] = B[j]; B[j] = C[j]; }
+        for (int j = 0; j < kItsPx + 2; ++j) { A[j] = B[j]; B[j] = C[j]; }
     }
 }
 
@@ -126,38 +140,46 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
     const int tx0 = (int)(blockIdx.x % a.tiles_x) * kItsTW;
     const int gy0 = ty0 - (k - 1);   // global row of staged row 0
     const int gx0 = tx0 - kItsHalo;  // global column of staged column 0
-    const int gx = gx0 + 4 * lane;   // the lane's first column
+    const int gx = gx0 + kItsPx * lane;  // the lane's first column
     const bool border = gy0 < 0 || gx0 < 0 || gy0 + TH2 > a.H || gx0 + kItsCols > a.W;
     const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(its_smem);
     const uint32_t sbuf_bytes = (uint32_t)TH2 * kItsCols * 4u;
-    const uint32_t lane_off = 16u * (uint32_t)lane;
+    const uint32_t lane_off = 4u * kItsPx * (uint32_t)lane;
 
     // Row r (staged coordinates) of round 0's input: global, clamped.
-    auto load_global = [&](int r, float v[6]) {
+    auto load_global = [&](int r, float v[kItsPx + 2]) {
         const float* row = a.in + (int64_t)clampi_its(gy0 + r, a.H) * a.in_pitch;
-        float4 q;
-        if (a.vec_in && gx >= 0 && gx + 3 < a.W) {
-            q = __ldg(reinterpret_cast<const float4*>(row + gx));
+        float4 q[kItsQ];
+        if (a.vec_in && gx >= 0 && gx + kItsPx - 1 < a.W) {
+#pragma unroll
+            for (int u = 0; u < kItsQ; ++u) q[u] = __ldg(reinterpret_cast<const float4*>(row + gx) + u);
         } else {
-            q.x = __ldg(row + clampi_its(gx, a.W));
-            q.y = __ldg(row + clampi_its(gx + 1, a.W));
-            q.z = __ldg(row + clampi_its(gx + 2, a.W));
-            q.w = __ldg(row + clampi_its(gx + 3, a.W));
+#pragma unroll
+            for (int u = 0; u < kItsQ; ++u) {
+                q[u].x = __ldg(row + clampi_its(gx + 4 * u, a.W));
+                q[u].y = __ldg(row + clampi_its(gx + 4 * u + 1, a.W));
+                q[u].z = __ldg(row + clampi_its(gx + 4 * u + 2, a.W));
+                q[u].w = __ldg(row + clampi_its(gx + 4 * u + 3, a.W));
+            }
         }
         its_widen(q, v);
     };
-    // The final round's rows go to the output tile (staged columns 8 .. 119, rows inside it).
-    const bool out_lane = lane >= kItsHalo / 4 && lane < (kItsHalo + kItsTW) / 4 && gx < a.W;
-    const bool out_vec = a.vec_out && gx + 3 < a.W;
-    auto emit_global = [&](int r, const float o[4]) {
+    // The final round's rows go to the output tile (the staged columns between the halos, rows
+    // inside the image).
+    const bool store_lane = lane >= kItsHalo / kItsPx && lane < (kItsHalo + kItsTW) / kItsPx;
+    const bool out_lane = store_lane && gx < a.W;
+    const bool out_vec = a.vec_out && gx + kItsPx - 1 < a.W;
+    auto emit_global = [&](int r, const float o[kItsPx]) {
         const int gy = gy0 + r;
         if (out_lane && gy < a.H) {
             float* orow = a.out + (int64_t)gy * a.out_pitch + gx;
             if (out_vec) {
-                *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+                for (int u = 0; u < kItsQ; ++u)
+                    reinterpret_cast<float4*>(orow)[u] = make_float4(o[4 * u], o[4 * u + 1], o[4 * u + 2], o[4 * u + 3]);
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < kItsPx; ++j)
                     if (gx + j < a.W) orow[j] = o[j];
             }
         }
@@ -167,13 +189,18 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
     // inside the image (with 16-byte aligned rows) take loads and stores with no clamp or bound
     // test: a per-lane test there is turned into predicated code that issues both paths.
     const bool fast = gy0 >= 1 && gy0 + TH2 + 1 <= a.H && gx0 >= 0 && gx0 + kItsCols <= a.W && a.vec_in && a.vec_out;
-    const bool store_lane = lane >= kItsHalo / 4 && lane < (kItsHalo + kItsTW) / 4;
-    auto load_global_fast = [&](int r, float v[6]) {
-        its_widen(__ldg(reinterpret_cast<const float4*>(a.in + (int64_t)(gy0 + r) * a.in_pitch + gx)), v);
+    auto load_global_fast = [&](int r, float v[kItsPx + 2]) {
+        const float4* row = reinterpret_cast<const float4*>(a.in + (int64_t)(gy0 + r) * a.in_pitch + gx);
+        float4 q[kItsQ];
+#pragma unroll
+        for (int u = 0; u < kItsQ; ++u) q[u] = __ldg(row + u);
+        its_widen(q, v);
     };
-    auto emit_global_fast = [&](int r, const float o[4]) {
+    auto emit_global_fast = [&](int r, const float o[kItsPx]) {
+        float4* orow = reinterpret_cast<float4*>(a.out + (int64_t)(gy0 + r) * a.out_pitch + gx);
         if (store_lane)
-            *reinterpret_cast<float4*>(a.out + (int64_t)(gy0 + r) * a.out_pitch + gx) = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+            for (int u = 0; u < kItsQ; ++u) orow[u] = make_float4(o[4 * u], o[4 * u + 1], o[4 * u + 2], o[4 * u + 3]);
     };
 
     for (int i = 0; i < k; ++i) {
@@ -184,9 +211,16 @@ __global__ void __launch_bounds__(kItsThreads) iterate_stencil_kernel(const __gr
         const int per = (hi - lo + kItsWarps - 1) / kItsWarps;
         const int r0 = lo + band * per;
         const int r1 = min(r0 + per, hi);
-        auto load_shared = [&](int r, float v[6]) { its_widen(its_lds128(src + (uint32_t)r * (kItsCols * 4)), v); };
-        auto emit_shared = [&](int r, const float o[4]) {
-            its_sts128(dst + (uint32_t)r * (kItsCols * 4), o[0], o[1], o[2], o[3]);
+        auto load_shared = [&](int r, float v[kItsPx + 2]) {
+            float4 q[kItsQ];
+#pragma unroll
+            for (int u = 0; u < kItsQ; ++u) q[u] = its_lds128(src + (uint32_t)r * (kItsCols * 4) + 16u * u);
+            its_widen(q, v);
+        };
+        auto emit_shared = [&](int r, const float o[kItsPx]) {
+#pragma unroll
+            for (int u = 0; u < kItsQ; ++u)
+                its_sts128(dst + (uint32_t)r * (kItsCols * 4) + 16u * u, o[4 * u], o[4 * u + 1], o[4 * u + 2], o[4 * u + 3]);
         };
         if (r0 < r1) {  // whole warp (r0, r1 depend on the band only)
             if (i == 0) {
