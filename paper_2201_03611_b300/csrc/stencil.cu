@@ -174,10 +174,11 @@ __device__ __forceinline__ void stencil_strip(const StencilArgs& a, int lane, in
 }
 
 // Register caps by measurement: K = 5 at 102 registers (20 warps per SM instead of 16; 7%
-// faster, the separable form 12%); K = 7 and 9 compiled with an explicit one-CTA minimum came
-// out 3-6% faster than with none; K = 3 already fits more warps and is slower under any cap.
+// faster, the separable form 12%); K = 9 at 168 (12 warps instead of 8, 72 bytes spilled;
+// 10% faster); K = 7 compiled with an explicit one-CTA minimum came out 3% faster than with
+// none; K = 3 already fits more warps and is slower under any cap.
 template <int K, bool SEP, typename TI, typename TO, bool ALIGNED>
-__global__ void __launch_bounds__(kStThreads, K == 5 ? 5 : (K >= 7 ? 1 : 0)) stencil_kernel(const __grid_constant__ StencilArgs a) {
+__global__ void __launch_bounds__(kStThreads, K == 5 ? 5 : (K == 9 ? 3 : (K == 7 ? 1 : 0))) stencil_kernel(const __grid_constant__ StencilArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (kStThreads / 32) + (threadIdx.x >> 5);
     if (gw >= a.nwarps) return;
