@@ -156,11 +156,11 @@ __device__ __forceinline__ void window_strip(const WindowArgs& wa, const Params&
     }
 }
 
-// 168 registers, 12 warps per SM instead of 8: K <= 5 fits without spilling (measured: K = 3
-// runs 1.5x, K = 5 1.1x faster than at 8 warps); K = 7 spills ~200 bytes per thread there and
-// is still 4% faster than at 8 warps.
+// Register caps by measurement: K = 3 at 128 registers (16 warps per SM, 36 bytes spilled; 16%
+// faster than at 12); K = 5 and 7 at 168 (12 warps instead of 8): K = 5 fits without spilling
+// (1.1x faster), K = 7 spills ~200 bytes per thread and is still 4% faster.
 template <typename TI, typename TO, int K, bool ALIGNED, bool TMA>
-__global__ void __launch_bounds__(kFwdThreads, 3) harris_window_kernel(const __grid_constant__ WindowArgs wa) {
+__global__ void __launch_bounds__(kFwdThreads, K <= 3 ? 4 : 3) harris_window_kernel(const __grid_constant__ WindowArgs wa) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const FwdArgs& a = wa.f;
     constexpr int NS = kFwdBulkStages;
