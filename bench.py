@@ -303,7 +303,8 @@ def run_ours(args, world, rank, local) -> dict | None:
         "roofline": {"bound": "hbm", "kernel": kern[dom]["kernel"], "achieved": kern[dom]["gb_s"], "peak": peak,
                      "unit": "GB/s", "frac": kern[dom]["gb_s"] / peak, "peak_kind": peak_kind,
                      "traffic": traffic,
-                     "algorithmic_bytes_per_launch": kern[dom]["algorithmic_bytes"]},
+                     "algorithmic_bytes_per_launch": kern[dom]["algorithmic_bytes"],
+                     "frac_of_nominal_8000": kern[dom]["gb_s"] / 8000.0},
         "kernels": kern,
         "fwd_gpix_s": kern["fwd"]["gpix_s"],
         "e2e": {"value": px / (e2e_ms * 1e-3) / 1e9 * world, "unit": "Gpixel/s", "h2d_bytes_per_step": h2d,
