@@ -103,7 +103,7 @@ int resident_warps(K kernel, int threads, size_t smem) {
 
 template <typename TI, typename TG>
 cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
-    constexpr int NS = kBwdStages;
+    constexpr int NS = bwd_stages<TI>();
     const size_t smem = (size_t)kBwdThreads * NS * (12 * sizeof(TI) + 4 * sizeof(TG)) + (kBwdThreads / 32) * NS * 8;
     const bool wr = a.rout != nullptr;
     void (*kern)(BwdArgs);
