@@ -35,7 +35,11 @@
  *
  * Errors.  Argument errors are detected on the host and returned before anything is
  * launched; launch failures come back as SHINE_ERR_CUDA (the CUDA error is then available
- * from shine_last_cuda_error). Calls are asynchronous on the given stream, never
+ * from shine_last_cuda_error). Fault injection for callers' error paths: with the environment
+ * variable SHINE_FAULT_INJECT="<call>=<status>[,...]" ("*" names every call), each named compute
+ * entry point returns that status (1..5) at once, before reading its arguments or touching the
+ * GPU. Each compute entry point also opens an NVTX range named after itself (free unless a
+ * profiler is attached). Calls are asynchronous on the given stream, never
  * synchronise, never allocate (except shine_plan_create), never throw, and are reentrant.
  * Gradients are OVERWRITTEN, not accumulated; a NULL gradient pointer skips that output.
  */

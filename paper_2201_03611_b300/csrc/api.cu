@@ -8,10 +8,12 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "harris_kernels.h"
 #include "shine.h"
+#include "entry.h"
 #include "shine_host.h"
 
 namespace shine {
@@ -102,6 +104,26 @@ int64_t bwd_max_warps(const Geometry& g) {
 
 bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+shine_status injected_fault(const char* name) {
+    const char* spec = std::getenv("SHINE_FAULT_INJECT");
+    if (spec == nullptr || *spec == '\0') return SHINE_OK;
+    const size_t nlen = std::strlen(name);
+    for (const char* p = spec; *p != '\0';) {
+        const char* end = std::strchr(p, ',');
+        if (end == nullptr) end = p + std::strlen(p);
+        const char* eq = static_cast<const char*>(std::memchr(p, '=', (size_t)(end - p)));
+        if (eq != nullptr) {
+            const size_t klen = (size_t)(eq - p);
+            if ((klen == 1 && *p == '*') || (klen == nlen && std::strncmp(p, name, nlen) == 0)) {
+                const int v = std::atoi(eq + 1);
+                if (v >= SHINE_ERR_INVALID_ARG && v <= SHINE_ERR_CUDA) return static_cast<shine_status>(v);
+            }
+        }
+        p = *end != '\0' ? end + 1 : end;
+    }
+    return SHINE_OK;
+}
+
 }  // namespace shine
 
 using namespace shine;
@@ -165,6 +187,7 @@ shine_status shine_output_shape(int64_t H, int64_t W, shine_border border, int64
 shine_status shine_pipeline_fwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
                                 shine_border border, const float* kappa, const float* wx, const float* wy,
                                 void* out, int64_t out_pitch, shine_dtype out_dt, void* stream) {
+    SHINE_ENTRY("shine_pipeline_fwd");
     if (!img || !kappa || !wx || !wy || !out) return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt) || !dtype_ok(out_dt)) return SHINE_ERR_INVALID_ARG;
     if (!(out_dt == dt || out_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
@@ -193,6 +216,7 @@ shine_status shine_corners(const void* img, int64_t H, int64_t W, int64_t img_pi
                            shine_border border, const float* kappa, const float* wx, const float* wy, float threshold,
                            uint8_t* mask, int64_t mask_pitch, void* out, int64_t out_pitch, shine_dtype out_dt,
                            void* stream) {
+    SHINE_ENTRY("shine_corners");
     if (!img || !kappa || !wx || !wy || !mask) return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt) || (out && !dtype_ok(out_dt))) return SHINE_ERR_INVALID_ARG;
     if (out && !(out_dt == dt || out_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
@@ -296,6 +320,7 @@ shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W, int64_t i
                                 const void* grad_out, int64_t gout_pitch, shine_dtype gout_dt, void* grad_img,
                                 int64_t gimg_pitch, float* grad_kappa, float* grad_wx, float* grad_wy,
                                 void* workspace, size_t ws_bytes, void* stream) {
+    SHINE_ENTRY("shine_pipeline_bwd");
     return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, gout_dt, nullptr, 0,
                    grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
 }
@@ -305,6 +330,7 @@ shine_status shine_pipeline_fwd_bwd(const void* img, int64_t H, int64_t W, int64
                                     const void* grad_out, int64_t gout_pitch, void* out, int64_t out_pitch,
                                     void* grad_img, int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
                                     float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+    SHINE_ENTRY("shine_pipeline_fwd_bwd");
     return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, dt, out, out_pitch,
                    grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
 }

@@ -22,6 +22,7 @@
 #include "harris_fwd_strip.cuh"
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 struct shine_plan {
     int n = 0;
@@ -299,6 +300,7 @@ extern "C" {
 
 shine_status shine_plan_create(const int64_t* HW, int32_t n, shine_dtype dt, shine_border border, int32_t mode,
                                const char* tune_cache_path, shine_plan** plan) {
+    SHINE_ENTRY("shine_plan_create");
     if (!HW || n <= 0 || !plan || !dtype_ok(dt) || !border_ok(border)) return SHINE_ERR_INVALID_ARG;
     if (mode != SHINE_MODE_FWD && mode != SHINE_MODE_FWD_BWD) return SHINE_ERR_INVALID_ARG;
     *plan = nullptr;
@@ -376,6 +378,7 @@ shine_status shine_plan_tile_rows(const shine_plan* plan, int32_t i, int32_t* ro
 shine_status shine_pipeline_batched(const shine_plan* plan, const shine_image_desc* descs, const float* kappa,
                                     const float* wx, const float* wy, float* grad_kappa, float* grad_wx,
                                     float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+    SHINE_ENTRY("shine_pipeline_batched");
     if (!plan || !descs || !kappa || !wx || !wy) return SHINE_ERR_INVALID_ARG;
     size_t need = 0;
     shine_plan_workspace(plan, &need);

@@ -17,6 +17,7 @@
 
 #include "harris_fwd_strip.cuh"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -258,6 +259,7 @@ extern "C" shine_status shine_harris_window(const void* img, int64_t H, int64_t 
                                             const float* kappa, const float* wx, const float* wy, int32_t K,
                                             const float* gv, const float* gh, void* out, int64_t out_pitch,
                                             shine_dtype out_dt, void* stream) {
+    SHINE_ENTRY("shine_harris_window");
     if (!img || !kappa || !wx || !wy || !gv || !gh || !out) return SHINE_ERR_INVALID_ARG;
     if (K != 3 && K != 5 && K != 7) return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt) || !dtype_ok(out_dt)) return SHINE_ERR_INVALID_ARG;

@@ -17,6 +17,7 @@
 #include "harris_kernels.h"
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -88,6 +89,7 @@ shine_status shine_pipeline_host(const void* img_h, const void* gout_h, void* ou
                                  int64_t W, shine_dtype dt, shine_border border, const float* kappa, const float* wx,
                                  const float* wy, float* grad_params, void* dev_img, void* dev_gout, void* dev_out,
                                  void* dev_gimg, void* workspace, size_t ws_bytes, int32_t nbands, void* stream) {
+    SHINE_ENTRY("shine_pipeline_host");
     if (!img_h || !gout_h || !kappa || !wx || !wy || !dev_img || !dev_gout || !dev_out || !dev_gimg)
         return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt) || nbands < 1 || nbands > kMaxBands) return SHINE_ERR_INVALID_ARG;

@@ -18,6 +18,7 @@
 
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -147,6 +148,7 @@ using namespace shine;
 
 extern "C" shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t n, int32_t k, shine_reduce_op op,
                                              float* out, void* stream) {
+    SHINE_ENTRY("shine_iterate_reduce");
     if (m < 0 || n < 1 || k < 0) return SHINE_ERR_INVALID_ARG;
     if (op != SHINE_REDUCE_SUM && op != SHINE_REDUCE_MAX && op != SHINE_REDUCE_MIN) return SHINE_ERR_INVALID_ARG;
     // n^k and n^(k-1) without overflow
@@ -174,5 +176,6 @@ extern "C" shine_status shine_iterate_reduce(const float* in, int64_t m, int32_t
 
 extern "C" shine_status shine_iterate_sum(const float* in, int64_t m, int32_t n, int32_t k, float* out,
                                           void* stream) {
+    SHINE_ENTRY("shine_iterate_sum");
     return shine_iterate_reduce(in, m, n, k, SHINE_REDUCE_SUM, out, stream);
 }

@@ -26,6 +26,7 @@
 
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -268,6 +269,7 @@ using namespace shine;
 extern "C" shine_status shine_iterate_stencil(const float* in, int64_t H, int64_t W, int64_t in_pitch,
                                               const float* weights, int32_t k, float* out, int64_t out_pitch,
                                               void* stream) {
+    SHINE_ENTRY("shine_iterate_stencil");
     if (!in || !out || !weights) return SHINE_ERR_INVALID_ARG;
     if (k < 1 || k > kItsMaxK) return SHINE_ERR_INVALID_ARG;
     if (H < 1 || W < 1 || H > kMaxDim || W > kMaxDim) return SHINE_ERR_INVALID_ARG;

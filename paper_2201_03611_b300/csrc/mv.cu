@@ -16,6 +16,7 @@
 
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -144,6 +145,7 @@ using namespace shine;
 
 extern "C" shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda, shine_dtype dt, const float* x,
                                  float* y, void* stream) {
+    SHINE_ENTRY("shine_mv");
     if (M < 0 || N < 0 || M > ((int64_t)1 << 31) || N > ((int64_t)1 << 31) || lda < std::max<int64_t>(N, 1))
         return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt)) return SHINE_ERR_INVALID_ARG;

@@ -13,6 +13,7 @@
 #include "harris_kernels.h"
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -58,6 +59,7 @@ extern "C" shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, i
                                                    int64_t gout_pitch, shine_dtype gout_dt, void* grad_img,
                                                    int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
                                                    float* grad_wy, void* stream) {
+    SHINE_ENTRY("shine_pipeline_bwd_noalloc");
     size_t need = 0;
     shine_status st = shine_pipeline_bwd_workspace(H, W, border, &need);
     if (st != SHINE_OK) return st;

@@ -22,6 +22,7 @@
 #include "harris_kernels.h"
 #include "shine.h"
 #include "shine_host.h"
+#include "entry.h"
 
 namespace shine {
 namespace {
@@ -243,6 +244,7 @@ extern "C" shine_status shine_stencil2d(const void* in, int64_t H, int64_t W, in
                                         shine_border border, int32_t K, const float* weights, const float* wv,
                                         const float* wh, void* out, int64_t out_pitch, shine_dtype out_dt,
                                         void* stream) {
+    SHINE_ENTRY("shine_stencil2d");
     if (!in || !out) return SHINE_ERR_INVALID_ARG;
     if (K < 1 || K > kStMaxK || K % 2 == 0) return SHINE_ERR_INVALID_ARG;
     const bool sep = weights == nullptr;
