@@ -258,7 +258,9 @@ def run_ours(args, world, rank, local) -> dict | None:
     gimg_pin = torch.empty(size, size, 3).pin_memory()
     par_pin = torch.empty(19).pin_memory()
     par = torch.empty(19, device=device)
-    nb = 16 if size >= 128 else 1
+    # row bands of the host pipeline: more bands shorten the pipeline's fill and drain, each adds a
+    # recomputed halo and launches (measured 8192^2: 16 bands 30.0 ms, 32 29.4, 48 29.2, 64 29.7)
+    nb = 48 if size >= 4096 else (16 if size >= 128 else 1)
     hws = torch.empty(S.ops.host_workspace_bytes(size, size, "clamp", nb), dtype=torch.uint8, device=device)
     e2e_steps = max(2, min(10, K))
 
