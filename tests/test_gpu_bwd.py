@@ -180,7 +180,8 @@ def test_bounded_waits_report_no_failure(shine):
 @pytest.mark.parametrize("shape,border,dtype,nbands", [((203, 517), "clamp", torch.float32, 16),
                                                        ((203, 517), "valid", torch.float32, 3),
                                                        ((96, 250), "clamp", torch.bfloat16, 5),
-                                                       ((64, 130), "clamp", torch.float32, 1)])
+                                                       ((64, 130), "clamp", torch.float32, 1),
+                                                       ((1030, 700), "clamp", torch.float32, 48)])
 def test_host_pipeline_matches_device_calls(shine, shape, border, dtype, nbands):
     """shine_pipeline_host (host buffers, band-pipelined copies) gives the device calls' R and
     d img bit for bit, and the same parameter cotangents within the summation bound."""
