@@ -188,6 +188,16 @@ def cpu_oracle_sample(img: torch.Tensor, g: torch.Tensor, kappa: float, rows: in
         cref.forward(b1[:1].contiguous(), kappa, wx, wy, "clamp", nthreads=cores)  # restore the thread count
         out["one_core"] = {"value": b1.shape[0] * b1.shape[1] / d1 / 1e9, "unit": "Gpixel/s",
                            "sample": f"rows 0..{single_core_rows - 1}, 1 thread ({d1:.2f} s)"}
+        # the pure-Python FP64 pattern oracle (nested lists), on the 256 x 256 VALID workload only
+        from oracle import harris as pattern_oracle
+        c1 = wl.plain_256()
+        nested = c1["img"].double().tolist()
+        t0 = time.perf_counter()
+        r1 = pattern_oracle.harris(nested, c1["kappa"], wx.double().tolist(), wy.double().tolist(), "valid")
+        dp = time.perf_counter() - t0
+        out["pattern_oracle_plain_256"] = {"value": len(r1) * len(r1[0]) / dp / 1e9, "unit": "Gpixel/s",
+                                           "sample": f"pure-Python pattern oracle, 256x256 VALID forward, "
+                                                     f"1 thread ({dp:.2f} s)"}
     return out
 
 
