@@ -5,8 +5,8 @@
 // double buffer live in shared memory, one pair per tile (temporal blocking):
 //   * a CTA owns a 64 x 112 output tile (default knobs below) and stages a 64 + 2(k-1) row by
 //     128 column region of every intermediate round (8 halo columns on each side, k-1 halo rows
-//     above and below: a
-//     round reaches one row and one column further, and round 0 reads its own row halo);
+//     above and below: a round reaches one row and one column further, and round 0 reads its
+//     own row halo);
 //   * round 0 reads the input straight from global memory (no copy into the double buffer:
 //     clamped loads, through L1), rounds 1 .. k-2 ping-pong between the two buffers, and round
 //     k-1 writes the output tile to global memory -- the swap / done structure of the paper's
