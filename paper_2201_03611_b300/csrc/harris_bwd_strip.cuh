@@ -108,11 +108,13 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
     const int xs = x - 4 * lane;
     constexpr uint32_t kImgBytes = kSegLoad * 3 * sizeof(TI), kCotBytes = kSegLoad * sizeof(TG);
     int last_issued = -1, last_done = -1;  // bulk staging: rows issued / waited for successfully
-    auto bulk_fetch = [&](int s) {
+    // ring position of the next row to stage, advanced one slot per step (no division per step)
+    uint32_t st_slot = TMA ? seq0 % NS : 0u, st_phase = TMA ? (seq0 / NS) & 1u : 0u;
+    auto bulk_fetch = [&](int s, uint32_t slot) {
         if constexpr (TMA) {
             if (s < nrows) last_issued = s;
             if (lane == 0 && s < nrows) {
-                const uint32_t q = seq0 + s, slot = q % NS, bar = bulk->bars + 8 * slot;
+                const uint32_t bar = bulk->bars + 8 * slot;
                 const int r = r_first + s, gy = r - 2;
                 const bool g_in = gy >= 0 && gy < a.gho;
                 fence_proxy_async_smem();
@@ -131,7 +133,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     if constexpr (TMA) {
 #pragma unroll
-        for (int s = 0; s < NS - 1; ++s) bulk_fetch(s);
+        for (int s = 0; s < NS - 1; ++s) bulk_fetch(s, (seq0 + s) % NS);
     } else {
 #pragma unroll
         for (int s = 0; s < NS - 1; ++s) {
@@ -145,24 +147,27 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     // Step s: gray row (6 wide, clamped) of image row r_first + s, and its cotangent row
     // (row - 2), staged NS - 1 steps ahead.
-    auto stage_in = [&](int s, float g6[6], float gv[4]) {
+    auto stage_in = [&](auto fast_tag, int s, float g6[6], float gv[4]) {
+        constexpr bool FAST_ROW = decltype(fast_tag)::value;
         const int r = r_first + s;
         float v[12];
         if constexpr (TMA) {
-            const uint32_t q = seq0 + s, slot = q % NS;
-            const bool ok = __all_sync(kFull, mbar_wait(bulk->bars + 8 * slot, (q / NS) & 1u));
+            const uint32_t slot = st_slot;
+            const bool ok = __all_sync(kFull, mbar_wait(bulk->bars + 8 * slot, st_phase));
+            if (++st_slot == (uint32_t)NS) { st_slot = 0; st_phase ^= 1u; }
             if (ok) last_done = s;
             else bulk->failed = true;
             rows.read(slot, clampi(r, H), v);
             const int gy = r - 2;
-            if (gy >= 0 && gy < a.gho) {
+            // fast steps of a bulk-staged (CLAMP) strip always have their cotangent row
+            if (FAST_ROW || (gy >= 0 && gy < a.gho)) {
                 grows.read(slot, r - 2, gv);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) gv[j] = 0.0f;
             }
             __syncwarp();  // every lane has read the slot that the next copy overwrites
-            if (ok) bulk_fetch(s + NS - 1);
+            if (ok) bulk_fetch(s + NS - 1, slot == 0 ? (uint32_t)NS - 1 : slot - 1);  // row s+NS-1 reuses row s-1's slot
         } else {
             cp_async_wait<NS - 2>();
             rows.read(s % NS, clampi(r, H), v);
@@ -199,8 +204,8 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         I0[j] = I1[j] = qa[j] = qb[j] = ga1[j] = ga2[j] = make_float2(0.0f, 0.0f);
         qaq[j] = qbq[j] = 0.0f;
     }
-    stage_in(0, G3, gv);  // image rows r_first, r_first + 1; shifted down at every step
-    stage_in(1, G4, gv);
+    stage_in(std::false_type{}, 0, G3, gv);  // image rows r_first, r_first + 1; shifted down at every step
+    stage_in(std::false_type{}, 1, G4, gv);
 
     TI* gimg = static_cast<TI*>(a.gimg);
     const float kc[3] = {kGrayR, kGrayG, kGrayB};
@@ -222,7 +227,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
         // shift the gray window down one row and stage row r into G4
 #pragma unroll
         for (int i = 0; i < 6; ++i) { G0[i] = G1[i]; G1[i] = G2[i]; G2[i] = G3[i]; G3[i] = G4[i]; }
-        stage_in(s, G4, gv);
+        stage_in(fast_tag, s, G4, gv);
 
         // B1: I at row r-1 (gray rows r-2, r-1, r).
         float2 I2[4];

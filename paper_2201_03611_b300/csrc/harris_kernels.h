@@ -51,8 +51,8 @@ constexpr int kFwdBulkStages = SHINE_FWD_BULK_STAGES;
 constexpr int kBwdThreads = 128;
 constexpr int kBwdStages = SHINE_BWD_STAGES;
 #ifndef SHINE_BWD_STAGES_F32
-#define SHINE_BWD_STAGES_F32 6    // the single-image adjoint's ring for float32 images (measured:
-#endif                            // 6 rows 0.448 ms, 5 0.453, 7 0.458, 8 0.454 on 8192^2)
+#define SHINE_BWD_STAGES_F32 7    // the single-image adjoint's ring for float32 images (measured:
+#endif                            // 7 rows 0.426 ms, 5 0.433, 6 0.431, 8 0.432 on 8192^2)
 template <typename TI> constexpr int bwd_stages() { return sizeof(TI) == 4 ? SHINE_BWD_STAGES_F32 : kBwdStages; }
 
 constexpr int kParamSlots = 19;   // d kappa, d Wx[9], d Wy[9]
