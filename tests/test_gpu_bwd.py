@@ -93,6 +93,20 @@ def test_diff_2048_full(shine):
     U.assert_params((dgk, dgwx, dgwy), ref[1:])
 
 
+def test_salt_8192_full(shine):
+    """The benchmark's adjoint workload (8192 x 8192 salt image, N(0,1) cotangent from seed 1, in
+    the launch configuration the benchmark times) against the oracle's full FP64 gradient."""
+    img = wl.salt_8192()["img"]
+    g = wl.random_cotangent(8192, 8192, seed=1)
+    wx, wy = wl.sobel_weights()
+    dgi, dgk, dgwx, dgwy = _run_bwd(shine, img, g, wl.KAPPA, wx, wy, "clamp")
+    torch.cuda.synchronize()
+    dgi = U.host(dgi)
+    ref = cref.backward(img, g, wl.KAPPA, wx, wy, "clamp", with_abs=True)
+    assert U.rel(dgi, ref[0]) <= U.TOL_GIMG
+    U.assert_params((dgk, dgwx, dgwy), ref[1:])
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_bwd_16bit_storage(shine, dtype):
     img = wl.random_image(130, 367, seed=3, dtype=dtype)
