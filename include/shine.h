@@ -166,7 +166,9 @@ SHINE_API shine_status shine_pipeline_host(const void* img_h, const void* gout_h
  * address (once per device, with that device current); make that first call before any stream
  * capture. All calls share the one array: calls whose GPU work can overlap in time (different
  * streams without ordering between them, or several host threads) race on it and give wrong
- * cotangents; serialise them on one stream. Nothing needs clearing between calls.
+ * cotangents; serialise them on one stream. Nothing needs clearing between calls. A bounded
+ * wait that gives up (results invalid) is reported through shine_wait_status, like the calls
+ * without a workspace, not through shine_workspace_status.
  */
 SHINE_API shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, int64_t W, int64_t img_pitch,
                                     shine_dtype dt, shine_border border, const float* kappa,
@@ -356,9 +358,9 @@ SHINE_API shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda
  * Bounded waits. Every wait of the kernels on a bulk copy polls its barrier a bounded number of
  * times; a wait that gives up stops its warp's work (the results of that call are invalid) and
  * sets a flag instead of hanging the GPU. Calls with a workspace (the backward passes) report it
- * through shine_workspace_status; the forward, corner and window calls set one library-wide
- * flag per GPU, read (and cleared when clear != 0) by shine_wait_status. Both synchronise with
- * the device.
+ * through shine_workspace_status; the forward, corner and window calls and
+ * shine_pipeline_bwd_noalloc set one library-wide flag per GPU, read (and cleared when
+ * clear != 0) by shine_wait_status. Both synchronise with the device.
  */
 SHINE_API shine_status shine_wait_status(int* failed, int clear);
 

@@ -258,11 +258,12 @@ shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_border bor
 
 namespace shine {
 
-static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
-                            shine_border border, const float* kappa, const float* wx, const float* wy,
-                            const void* grad_out, int64_t gout_pitch, shine_dtype gout_dt, void* out,
-                            int64_t out_pitch, void* grad_img, int64_t gimg_pitch, float* grad_kappa,
-                            float* grad_wx, float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
+shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
+                     shine_border border, const float* kappa, const float* wx, const float* wy,
+                     const void* grad_out, int64_t gout_pitch, shine_dtype gout_dt, void* out,
+                     int64_t out_pitch, void* grad_img, int64_t gimg_pitch, float* grad_kappa,
+                     float* grad_wx, float* grad_wy, void* workspace, size_t ws_bytes, void* stream,
+                     unsigned int* err_word) {
     if (!img || !kappa || !wx || !wy || !grad_out) return SHINE_ERR_INVALID_ARG;
     if (!dtype_ok(dt) || !dtype_ok(gout_dt)) return SHINE_ERR_INVALID_ARG;
     if (!(gout_dt == dt || gout_dt == SHINE_F32)) return SHINE_ERR_UNSUPPORTED;
@@ -288,7 +289,8 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     a.gout = grad_out; a.gout_pitch = gout_pitch; a.gho = (int)Ho; a.gwo = (int)Wo;
     a.gimg = grad_img; a.gimg_pitch = gimg_pitch;
     a.kappa = kappa; a.wx = wx; a.wy = wy;
-    a.err = static_cast<unsigned int*>(workspace);
+    // bounded-wait failures go to the workspace header (cleared below), or to err_word when given
+    a.err = err_word != nullptr ? err_word : static_cast<unsigned int*>(workspace);
     a.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + kWorkspaceHeader);
     a.pstride = 0;
     a.poffset = 0;
@@ -301,8 +303,10 @@ static shine_status run_bwd(const void* img, int64_t H, int64_t W, int64_t img_p
     a.rout = out; a.rout_pitch = out_pitch;
     a.rout_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * si) && ((size_t)out_pitch * si) % (4 * si) == 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    st = cuda_status(cudaMemsetAsync(a.err, 0, sizeof(unsigned int), s));
-    if (st != SHINE_OK) return st;
+    if (err_word == nullptr) {
+        st = cuda_status(cudaMemsetAsync(a.err, 0, sizeof(unsigned int), s));
+        if (st != SHINE_OK) return st;
+    }
     int used = 0;
     st = cuda_status(launch_harris_bwd(a, dt, gout_dt, (int)max_warps, s, &used));
     if (st != SHINE_OK) return st;
@@ -322,7 +326,7 @@ shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W, int64_t i
                                 void* workspace, size_t ws_bytes, void* stream) {
     SHINE_ENTRY("shine_pipeline_bwd");
     return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, gout_dt, nullptr, 0,
-                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
+                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream, nullptr);
 }
 
 shine_status shine_pipeline_fwd_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch, shine_dtype dt,
@@ -332,7 +336,7 @@ shine_status shine_pipeline_fwd_bwd(const void* img, int64_t H, int64_t W, int64
                                     float* grad_wy, void* workspace, size_t ws_bytes, void* stream) {
     SHINE_ENTRY("shine_pipeline_fwd_bwd");
     return run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, dt, out, out_pitch,
-                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream);
+                   grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, workspace, ws_bytes, stream, nullptr);
 }
 
 }  // extern "C"

@@ -60,6 +60,7 @@ extern "C" shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, i
                                                    int64_t gimg_pitch, float* grad_kappa, float* grad_wx,
                                                    float* grad_wy, void* stream) {
     SHINE_ENTRY("shine_pipeline_bwd_noalloc");
+    if (!img || !kappa || !wx || !wy || !grad_out) return SHINE_ERR_INVALID_ARG;  // before touching a GPU
     size_t need = 0;
     shine_status st = shine_pipeline_bwd_workspace(H, W, border, &need);
     if (st != SHINE_OK) return st;
@@ -67,9 +68,13 @@ extern "C" shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, i
     void* partials = nullptr;
     st = shine::partials_on_current_device(&partials);
     if (st != SHINE_OK) return st;
+    unsigned int* flag = shine::wait_flag();
+    if (flag == nullptr) return SHINE_ERR_CUDA;
     // Every launch writes all the partial sums its finalize step reads, so nothing left in the
-    // array by an earlier call is ever used and nothing needs clearing.
-    return shine_pipeline_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, gout_dt,
-                              grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, partials, shine::kNoAllocBytes,
-                              stream);
+    // array by an earlier call is ever used and nothing needs clearing. A bounded wait that gives
+    // up is reported in the library-wide flag that shine_wait_status reads (the caller has no
+    // workspace to pass to shine_workspace_status).
+    return shine::run_bwd(img, H, W, img_pitch, dt, border, kappa, wx, wy, grad_out, gout_pitch, gout_dt, nullptr, 0,
+                          grad_img, gimg_pitch, grad_kappa, grad_wx, grad_wy, partials, shine::kNoAllocBytes, stream,
+                          flag);
 }

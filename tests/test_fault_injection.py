@@ -57,6 +57,24 @@ def test_wildcard_and_malformed_specs(L, inject):
         assert _fwd_null(L) == 1, bad
 
 
+def _noalloc_null(L):
+    v = ctypes.c_void_p
+    return L.shine_pipeline_bwd_noalloc(None, 8, 8, 24, 0, 1, v(4096), v(4096), v(4096), v(4096), 8, 0, None, 24,
+                                        None, None, None, None)
+
+
+def test_noalloc_is_targeted_on_its_own(L, inject):
+    # the no-allocation backward consults the injector once, under its own name: injecting into
+    # shine_pipeline_bwd leaves it alone, and injecting into it leaves shine_pipeline_bwd alone
+    v = ctypes.c_void_p
+    bwd_null = lambda: L.shine_pipeline_bwd(None, 8, 8, 24, 0, 1, v(4096), v(4096), v(4096), v(4096), 8, 0, None, 24,
+                                            None, None, None, None, 0, None)
+    inject("shine_pipeline_bwd=5")
+    assert bwd_null() == 5 and _noalloc_null(L) == 1
+    inject("shine_pipeline_bwd_noalloc=4")
+    assert bwd_null() == 1 and _noalloc_null(L) == 4
+
+
 def test_binding_raises_shine_error(L, inject):
     from paper_2201_03611_b300 import _lib
     inject("shine_mv=5")

@@ -3,8 +3,12 @@
 A caller that is only handed its input and output buffers (or that must not allocate after
 start-up) cannot supply the workspace shine_pipeline_bwd asks for; this entry keeps the
 partial sums in a fixed array inside the library instead. Here it is called through the C ABI
-twice in a row, on different images, and each result is checked against the workspace-taking
-entry point on the same inputs. This file is collected last on purpose.
+twice in a row, on different images, and each result must equal, bit for bit, the
+workspace-taking entry point's on the same inputs: both run the same kernel with the same warp
+count and the same fixed-order float64 finalize, so any difference would be a stale or shared
+partial sum. A bounded wait that gave up would be reported through shine_wait_status, which
+must stay clear. (The array's size limit, SHINE_ERR_UNSUPPORTED, needs a GPU with more than 256
+SMs to reach and is not exercised here.) This file is collected last on purpose.
 """
 import ctypes
 
@@ -38,6 +42,7 @@ def _noalloc(img, g, k, wx, wy, border):
                                    [((64, 124), "clamp", torch.bfloat16), ((300, 301), "clamp", torch.float32)]])
 def test_noalloc_matches_workspace_entry_on_two_calls_in_a_row(calls):
     import paper_2201_03611_b300 as S
+    S.ops.wait_failed(clear=True)  # start from a clear bounded-wait flag
     for n, ((h, w), border, dtype) in enumerate(calls):
         img = wl.random_image(h, w, seed=40 + n).to(dtype).cuda()
         ho, wo = S.output_shape(h, w, border)
@@ -46,6 +51,6 @@ def test_noalloc_matches_workspace_entry_on_two_calls_in_a_row(calls):
         got = _noalloc(img, g, k, wx, wy, border)
         ref = S.pipeline_bwd(img, g, k, wx, wy, border)
         torch.cuda.synchronize()
-        assert U.rel(U.host(got[0]), U.host(ref[0])) <= U.TOL_GIMG
-        for a, b in zip(got[1:], ref[1:]):
-            assert U.rel(U.host(a), U.host(b)) <= U.TOL_F32
+        for name, a, b in zip(("d img", "d kappa", "d Wx", "d Wy"), got, ref):
+            assert torch.equal(a, b), (n, name)
+    assert not S.ops.wait_failed(clear=True)
