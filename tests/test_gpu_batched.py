@@ -145,3 +145,67 @@ def test_tune_cache_is_honoured(shine, tmp_path):
     path.write_text(f"# test\n{gpu_key()} 1 1 3 7 24\n{gpu_key()} 1 1 3 10 200\n")
     plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=str(path))
     assert [plan.tile_rows(i) for i in range(3)] == [24, 200, 33]
+
+
+def test_batched_512_workload_with_tuned_tiles(shine):
+    """The benchmark's own uneven batch in the benchmark's launch configuration: the 512 bf16
+    images (sizes log-uniform in [64, 2048], seed 2), the committed tuning cache (tall bands of
+    512 and 1024 rows on the large images, so multi-band images occur), one persistent launch
+    replayed from a CUDA graph. Every image's R, d img and d kappa_i against the FP64 oracle on
+    the quantised input, d Wx and d Wy against the oracle's sums over the batch, and R and d img
+    bit-equal to per-image fused calls."""
+    cache = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2201_03611_b300",
+                         "tune_cache.txt")
+    b = wl.batch_512()
+    n = len(b["imgs"])
+    imgs = [t.cuda() for t in b["imgs"]]
+    gouts = [t.cuda() for t in b["ws"]]
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=cache)
+    default = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True)
+    rows = [plan.tile_rows(i) for i in range(n)]
+    assert rows != [default.tile_rows(i) for i in range(n)], "tuning cache not picked up on this GPU"
+    big = [i for i, (h, _) in enumerate(shapes) if h >= 1024]
+    assert big and any(shapes[i][0] > rows[i] for i in big), "no multi-band image in the batch"
+    outs = [torch.empty(h, w, dtype=torch.bfloat16, device="cuda") for h, w in shapes]
+    gimgs = [torch.empty_like(t) for t in imgs]
+    descs = plan.bind(imgs, outs, gouts, gimgs)
+    ws_buf = plan.new_workspace("cuda")
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.sobel_weights()]
+    gk = torch.empty(n, device="cuda")
+    gwx, gwy = torch.empty(3, 3, device="cuda"), torch.empty(3, 3, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws_buf)
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws_buf)
+    for t in outs + gimgs:
+        t.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    swx, swy = np.zeros((3, 3)), np.zeros((3, 3))
+    awx, awy = np.zeros((3, 3)), np.zeros((3, 3))
+    gk_h = U.host(gk)
+    for i in range(n):
+        r, gi, _, _, _ = shine.pipeline_fwd_bwd(imgs[i], gouts[i], kappa[i:i + 1].contiguous(), wx, wy, "clamp")
+        assert torch.equal(outs[i], r), i
+        assert torch.equal(gimgs[i], gi), i
+        ki = float(b["kappa"][i])
+        ref = cref.forward(b["imgs"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp")
+        assert U.rel(U.host(outs[i]), ref) <= U.TOL_16, i
+        gref, gki, gwxi, gwyi, absi = cref.backward(b["imgs"][i], b["ws"][i], ki, wl.SOBEL_X, wl.SOBEL_Y, "clamp",
+                                                    with_abs=True)
+        assert U.rel(U.host(gimgs[i]), gref) <= U.TOL_16, i
+        assert abs(gk_h[i] - gki) <= U.TOL_PARAM_COND * absi[0], i
+        swx += gwxi
+        swy += gwyi
+        awx += absi[1]
+        awy += absi[2]
+    U.assert_params((gk[:1], gwx, gwy), (float(gk_h[0]), swx, swy, (1.0, awx, awy)))
+    plan.close()
+    default.close()

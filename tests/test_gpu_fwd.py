@@ -119,3 +119,36 @@ def test_salt_8192_sampled(shine):
     assert U.rel(got, ref) <= U.TOL_F32
     out2 = shine.pipeline_fwd(dimg * 2, k, dwx, dwy, "clamp")
     assert torch.equal(out2, out * 16)
+
+
+def test_diff_2048_full_map(shine):
+    """The 2048 x 2048 differentiation image, CLAMP, float32: the whole response map against the
+    oracle element by element (16-byte aligned rows: bulk-staged interior segments, register-staged
+    edge segments), with the default and with random non-symmetric weights."""
+    cfg = wl.diff_2048()
+    for ww in (wl.sobel_weights(), wl.random_weights(31)):
+        ref = cref.forward(cfg["img"], wl.KAPPA, *ww, "clamp")
+        k, dwx, dwy = U.dev_params(wl.KAPPA, *ww)
+        out = shine.pipeline_fwd(cfg["img"].cuda(), k, dwx, dwy, "clamp")
+        torch.cuda.synchronize()
+        assert U.rel(U.host(out), ref) <= U.TOL_F32
+
+
+def test_salt_8192_full_rows(shine):
+    """The 8192 x 8192 salt workload in the benchmark's launch configuration, compared element by
+    element over three bands of 600 whole rows (the top, the middle and the bottom of the image).
+    At this size each warp streams a strip of about 250 rows, so the staging ring's slots and
+    phases wrap many times within a strip, and strips end and start inside every band. The oracle
+    runs on each band as an image of its own; R of a band's image equals R of the full image
+    except within 2 rows of a cut (the clamp), so those rows are left out."""
+    cfg = wl.salt_8192()
+    img = cfg["img"]
+    wx, wy = wl.sobel_weights()
+    k, dwx, dwy = U.dev_params(cfg["kappa"], wx, wy)
+    out = U.host(shine.pipeline_fwd(img.cuda(), k, dwx, dwy, "clamp"))
+    n = 600
+    for a in (0, 4096 - n // 2, 8192 - n):
+        ref = cref.forward(img[a:a + n].contiguous(), cfg["kappa"], wx, wy, "clamp")
+        lo = 0 if a == 0 else 2
+        hi = n if a + n == 8192 else n - 2
+        assert U.rel(out[a + lo:a + hi], ref[lo:hi]) <= U.TOL_F32, a
