@@ -1,33 +1,185 @@
 // Fused forward kernel: A1 gray -> A2 Sobel -> A3 products -> A4 box sum -> A5 response,
 // with only the response written to global memory (the paper's map-fusion and fuseReduceMap
 // rules, Sec. 4.2, applied to the whole pipeline; toMem(Global) of the result, Sec. 5.3).
-// One warp streams one (column segment, row band); see harris_fwd_strip.cuh.
+// One warp streams one (column segment, row band), eight columns per lane; see
+// harris_fwd_wide.cuh.
 #include <algorithm>
+#include <type_traits>
 
-#include "harris_fwd_strip.cuh"
+#include "harris_fwd_wide.cuh"
 
 namespace shine {
 
 namespace {
 
-template <typename TI, typename TO, int D, bool ALIGNED, bool TMA>
-__global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_kernel(FwdArgs a) {
+// Stores of R: 16-byte stores on lanes whose 8 columns are all output columns of a row that
+// allows them, else element by element.
+template <typename TO>
+__device__ __forceinline__ void store_row(const FwdArgs& a, TO* orow, int x, bool vec, const float R[8]) {
+    if (vec && x >= a.xlo && x + kWCols <= a.xhi) {
+        store8(orow + (x - a.ox), R);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kWCols; ++j) {
+            const int c = x + j;
+            if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
+        }
+    }
+}
+
+// Stores of R on an interior segment (no output offset, every column an output column).
+template <typename TO>
+__device__ __forceinline__ void store_row_interior(const FwdArgs& a, TO* p, const float R[8]) {
+    if (a.out_vec) {
+        store8(p, R);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kWCols; ++j) p[j] = Conv<TO>::st(R[j]);
+    }
+}
+
+// Forward strip of an image whose rows are not 16-byte aligned: each lane loads its pixels of
+// the next row element by element, one row ahead.
+template <typename TI, typename TO, bool EDGE>
+__device__ __forceinline__ void wide_strip_elem(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
+    const int H = a.H, W = a.W;
+    const TI* img = static_cast<const TI*>(a.img);
+    TO* out = static_cast<TO*>(a.out);
+    const bool producer = lane >= 1 && lane <= 30;
+    int row = y0 - 2;  // image row (unclamped) of the next gray row
+    WideRaw<TI> buf;
+    wide_load<TI, false>(img, a.img_pitch, clampi(row, H), x, W, buf);
+    auto take = [&](float g10[10]) {
+        float c[8];
+        gray8<TI>(buf, c);
+        ++row;
+        wide_load<TI, false>(img, a.img_pitch, clampi(row, H), x, W, buf);
+        widen10<EDGE>(c, g10, x, W);
+    };
+    auto store = [&](int y, const float R[8]) {
+        if (producer) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+    };
+    wide_strip_core<EDGE>(P, x, W, H, y0, y1, take, store, [] { return true; });
+}
+
+// Forward strip of a 16-byte aligned image staged in registers: each lane loads its 8 pixels of
+// the next row with 16-byte loads one row ahead (element by element where a lane straddles the
+// image edge), and lane 0 prefetches the warp's span of the row kPfRows ahead into L2 with one
+// bulk prefetch, so the register loads hit L2. Nothing waits on the prefetch.
+template <typename TI, typename TO, bool EDGE>
+__device__ __forceinline__ void wide_strip_pf(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
+    constexpr int K = kWidePfRows;
+    const int H = a.H, W = a.W;
+    const TI* img = static_cast<const TI*>(a.img);
+    TO* out = static_cast<TO*>(a.out);
+    const bool producer = lane >= 1 && lane <= 30;
+    // the warp's 256 staged pixels clipped to the image, in whole 16-byte chunks
+    const int xs = x - kWCols * lane;
+    const int plo = xs < 0 ? 0 : xs, phi = xs + kWSegLoad < W ? xs + kWSegLoad : W;
+    const uint32_t pbytes = (uint32_t)((phi - plo) * 3 * (int)sizeof(TI)) & ~15u;
+    const char* prow = reinterpret_cast<const char*>(img + (int64_t)plo * 3);
+    const int64_t pitch_b = a.img_pitch * (int64_t)sizeof(TI);
+    int pr = y0 - 2;  // next row to prefetch (unclamped)
+    const uint32_t lead = lane == 0 && pbytes != 0;
+    auto prefetch_next = [&]() {
+        prefetch_l2_pred(lead && pr >= 0 && pr < H, prow + (int64_t)(pr < 0 ? 0 : pr) * pitch_b, pbytes);
+        ++pr;
+    };
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) prefetch_next();
+    int row = y0 - 2;  // image row (unclamped) of the next gray row
+    WideRaw<TI> buf;
+    wide_load<TI, true, !EDGE>(img, a.img_pitch, clampi(row, H), x, W, buf);
+    auto take = [&](float g10[10]) {
+        float c[8];
+        gray8<TI>(buf, c);
+        ++row;
+        wide_load<TI, true, !EDGE>(img, a.img_pitch, clampi(row, H), x, W, buf);  // one row ahead
+        prefetch_next();
+        widen10<EDGE>(c, g10, x, W);
+    };
+    auto store = [&](int y, const float R[8]) {
+        if (producer) {
+            if constexpr (EDGE) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+            else store_row_interior(a, out + (int64_t)y * a.out_pitch + x, R);
+        }
+    };
+    wide_strip_core<EDGE>(P, x, W, H, y0, y1, take, store, [] { return true; });
+}
+
+// Forward strip of an edge segment of a 16-byte aligned image, staged per lane by cp.async.
+template <typename TI, typename TO, int NS>
+__device__ __forceinline__ void wide_strip_edge(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                                uint32_t ring0) {
+    const int H = a.H, W = a.W;
+    TO* out = static_cast<TO*>(a.out);
+    const bool producer = lane >= 1 && lane <= 30;
+    const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    WideLaneStage<TI, NS> src(static_cast<const TI*>(a.img), a.img_pitch, x, W, H, ring0, lane, y0 - 2, n);
+    auto take = [&](float g10[10]) {
+        WideRaw<TI> r;
+        src.take_raw(r);
+        float c[8];
+        gray8<TI>(r, c);
+        widen10<true>(c, g10, x, W);
+    };
+    auto store = [&](int y, const float R[8]) {
+        if (producer) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+    };
+    wide_strip_core<true>(P, x, W, H, y0, y1, take, store, [] { return true; });
+    src.finish();
+}
+
+// Forward strip of an interior segment of a 16-byte aligned image, staged by bulk copies.
+template <typename TI, typename TO, int NS>
+__device__ __forceinline__ void wide_strip_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                                uint32_t ring0, WideBulkState& bs) {
+    const int H = a.H;
+    const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    WideBulk<TI, NS> src(bs, static_cast<const TI*>(a.img), a.img_pitch, x - kWCols * lane, ring0, lane, y0 - 2, n, H);
+    TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
+    const int64_t opitch = a.out_pitch;
+    const bool producer = lane >= 1 && lane <= 30;
+    auto take = [&](float g10[10]) {
+        WideRaw<TI> r;
+        src.take_raw(r);
+        float c[8];
+        gray8<TI>(r, c);
+        widen10<false>(c, g10, x, 0);
+    };
+    auto store = [&](int, const float R[8]) {
+        if (producer) store_row_interior(a, orow, R);
+        orow += opitch;
+    };
+    wide_strip_core<false>(P, x, a.W, H, y0, y1, take, store, [&] { return !bs.failed; });
+    src.finish();
+}
+
+// Staging by bulk copies into a shared-memory ring (interior segments) or in registers with L2
+// prefetch, per storage type; chosen by measurement.
+template <typename TI> constexpr bool wide_bulk() { return sizeof(TI) == 4 ? SHINE_WIDE_BULK_F32 : SHINE_WIDE_BULK_16; }
+
+// ALIGNED: the image rows are 16-byte aligned: interior segments are staged by bulk copies
+// (wide_bulk) or in registers with L2 prefetch, edge segments in registers with L2 prefetch;
+// otherwise every lane loads its pixels element by element.
+template <typename TI, typename TO, bool SMEM>
+__global__ void __launch_bounds__(kFwdThreads, SHINE_WIDE_MIN_BLOCKS) harris_fwd_kernel(FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int NS = kFwdBulkStages;
+    constexpr int NS = SHINE_WIDE_BULK_STAGES;
+    constexpr uint32_t kSlotBytes = kWSegLoad * 3 * sizeof(TI);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kFwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
-    FwdBulk bulk;
-    bulk.seq = 0;
-    bulk.failed = false;
-    TI* ring = nullptr;
-    if constexpr (TMA) {
-        ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
-        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdThreads * NS * 12 * sizeof(TI)) + warp * NS;
-        bulk.bars = smem_u32(bars);
+    WideBulkState bs;
+    bs.seq = 0;
+    bs.failed = false;
+    uint32_t ring0 = 0;
+    if constexpr (SMEM && wide_bulk<TI>()) {
+        ring0 = smem_u32(smem_raw) + (uint32_t)warp * NS * kSlotBytes;
+        bs.bars = smem_u32(smem_raw) + (uint32_t)(kFwdThreads / 32) * NS * kSlotBytes + (uint32_t)warp * NS * 8;
         if (lane == 0)
-            for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+            for (int i = 0; i < NS; ++i) mbar_init(bs.bars + 8 * i, 1);
         mbar_init_fence();
         __syncwarp();
     }
@@ -37,19 +189,29 @@ __global__ void __launch_bounds__(kFwdThreads, SHINE_FWD_MIN_BLOCKS) harris_fwd_
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
     warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
-    while (lo < hi && !bulk.failed) {
+    while (lo < hi && !bs.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
         const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
-        const int xb = a.x0 + seg * kSegOut;
-        const int x = xb - 4 + 4 * lane;
-        const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W) || a.valid;
-        if (edge) fwd_strip<TI, TO, kFwdEdgeStages, true, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
-        else if constexpr (TMA) fwd_strip_bulk<TI, TO, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring, bulk);
-        else fwd_strip<TI, TO, D, false, ALIGNED>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+        const int xb = a.x0 + seg * kWSegOut;
+        const int x = xb - kWCols + kWCols * lane;
+        const bool edge = (xb - kWCols < 0) || (xb + kWSegOut + kWCols > a.W) || a.valid;
+        if constexpr (SMEM) {
+            if constexpr (wide_bulk<TI>()) {
+                if (!edge) wide_strip_bulk<TI, TO, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring0, bs);
+                else if constexpr (SHINE_WIDE_EDGE_LANES) wide_strip_edge<TI, TO, NS>(a, P, lane, x, a.ylo + r0, a.ylo + r1, ring0);
+                else wide_strip_pf<TI, TO, true>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+            } else {
+                if (edge) wide_strip_pf<TI, TO, true>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+                else wide_strip_pf<TI, TO, false>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+            }
+        } else {
+            if (edge) wide_strip_elem<TI, TO, true>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+            else wide_strip_elem<TI, TO, false>(a, P, lane, x, a.ylo + r0, a.ylo + r1);
+        }
         lo += r1 - r0;
     }
-    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
+    if (bs.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
 }
 
 template <typename K>
@@ -65,15 +227,17 @@ int resident_warps(K kernel, int threads, size_t smem) {
 
 template <typename TI, typename TO>
 cudaError_t launch_fwd_t(FwdArgs a, cudaStream_t s) {
-    constexpr int D = kFwdStages;
-    constexpr int NS = kFwdBulkStages;
-    const bool tma = a.tma && a.aligned && a.out_vec;  // the bulk strips store R with vector stores
-    const size_t smem = tma ? (size_t)kFwdThreads * NS * 12 * sizeof(TI) + (kFwdThreads / 32) * NS * 8 : 0;
-    auto kern = tma ? harris_fwd_kernel<TI, TO, D, true, true>
-                    : (a.aligned ? harris_fwd_kernel<TI, TO, D, true, false> : harris_fwd_kernel<TI, TO, D, false, false>);
+    constexpr int NS = SHINE_WIDE_BULK_STAGES;
+    // shared-memory staging needs 16-byte aligned image rows (bulk copies, 16-byte cp.async)
+    const bool smem_stage = a.tma;
+    const size_t smem = smem_stage && wide_bulk<TI>() ? (size_t)(kFwdThreads / 32) * NS * (kWSegLoad * 3 * sizeof(TI) + 8) : 0;
+    auto kern = smem_stage ? harris_fwd_kernel<TI, TO, true> : harris_fwd_kernel<TI, TO, false>;
+    // the wide layout: segments of kWSegOut output columns, segment 0 at the storage type's origin
+    a.x0 = wide_origin<TI>();
+    a.nseg = (a.xhi - a.x0 + kWSegOut - 1) / kWSegOut;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     if (units <= 0) return cudaSuccess;
-    if (tma) {
+    if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -154,7 +154,8 @@ struct FwdArgs : Geometry {
     const float* wx;
     const float* wy;
     int aligned;  // image rows can be staged with 16 / 8-byte copies
-    int out_vec;  // output rows can be written with 16 / 8-byte stores
+    int out_vec;  // output rows can be written with vector stores: 16-byte aligned rows for the
+                  // forward kernel, 4-element aligned rows for the corner kernel
     int tma;      // interior segments may use bulk (TMA) staging (16-byte aligned rows)
     unsigned int* err;  // nonzero after a bounded wait gave up (nullable)
 };
@@ -220,6 +221,48 @@ constexpr size_t kWorkspaceHeader = 256;  // backward workspace: error word, the
 #endif
 #ifndef SHINE_BWD_SEGMENT_ORIGIN
 #define SHINE_BWD_SEGMENT_ORIGIN -76
+#endif
+// First output column of segment 0 in the forward kernel, whose segments are 240 output columns
+// wide (8 per lane), per storage type: any multiple of 8 in (-240, 0] makes every interior
+// segment's staged span (8 columns left of its output) start on a 16-byte boundary for float32
+// and 16-bit rows.
+#ifndef SHINE_WIDE_ORIGIN_F32
+#define SHINE_WIDE_ORIGIN_F32 -232
+#endif
+#ifndef SHINE_WIDE_ORIGIN_16
+#define SHINE_WIDE_ORIGIN_16 0
+#endif
+template <typename TI> constexpr int wide_origin() { return sizeof(TI) == 4 ? SHINE_WIDE_ORIGIN_F32 : SHINE_WIDE_ORIGIN_16; }
+static_assert(SHINE_WIDE_ORIGIN_F32 % 8 == 0 && SHINE_WIDE_ORIGIN_F32 > -240 && SHINE_WIDE_ORIGIN_F32 <= 0 &&
+              SHINE_WIDE_ORIGIN_16 % 8 == 0 && SHINE_WIDE_ORIGIN_16 > -240 && SHINE_WIDE_ORIGIN_16 <= 0,
+              "wide segment spans must start on 8-pixel boundaries");
+// Shared-memory slots of the forward's bulk staging ring (measured on 8192^2 float32: 4 slots
+// 0.173 ms, 6 slots 0.185 ms).
+#ifndef SHINE_WIDE_BULK_STAGES
+#define SHINE_WIDE_BULK_STAGES 4
+#endif
+// Edge segments of bulk-staged forward kernels: 1 = per-lane cp.async into the shared-memory ring,
+// 0 = registers with L2 prefetch.
+#ifndef SHINE_WIDE_EDGE_LANES
+#define SHINE_WIDE_EDGE_LANES 1
+#endif
+// Forward staging of interior segments per storage type: 1 = bulk copies into a shared-memory
+// ring, 0 = registers one row ahead with an L2 bulk prefetch kPfRows ahead (edge segments always
+// use the latter).
+#ifndef SHINE_WIDE_BULK_F32
+#define SHINE_WIDE_BULK_F32 1
+#endif
+#ifndef SHINE_WIDE_BULK_16
+#define SHINE_WIDE_BULK_16 0
+#endif
+#ifndef SHINE_WIDE_PF_ROWS
+#define SHINE_WIDE_PF_ROWS 4
+#endif
+constexpr int kWidePfRows = SHINE_WIDE_PF_ROWS;
+// Resident CTAs per SM the forward kernel's register budget must allow (3: 168 registers, 12
+// warps per SM).
+#ifndef SHINE_WIDE_MIN_BLOCKS
+#define SHINE_WIDE_MIN_BLOCKS 3
 #endif
 constexpr int kFwdSegmentOrigin = SHINE_FWD_SEGMENT_ORIGIN;
 constexpr int kBwdSegmentOrigin = SHINE_BWD_SEGMENT_ORIGIN;

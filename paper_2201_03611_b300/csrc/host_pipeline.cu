@@ -159,7 +159,7 @@ shine_status shine_pipeline_host(const void* img_h, const void* gout_h, void* ou
             f.img = dev_img; f.img_pitch = 3 * W; f.out = dev_out; f.out_pitch = Wo;
             f.kappa = kappa; f.wx = wx; f.wy = wy;
             f.aligned = (img_row % (si == 4 ? 16 : 8)) == 0;  // vector staging needs aligned rows
-            f.out_vec = border == SHINE_CLAMP && (Wo * si) % (4 * si) == 0;
+            f.out_vec = border == SHINE_CLAMP && (Wo * si) % 16 == 0 && aligned_to(dev_out, 16);
             f.tma = SHINE_FWD_TMA && (img_row % 16) == 0;
             f.err = wait_flag();
             SHINE_TRY(launch_harris_fwd(f, dt, dt, ds->comp));
