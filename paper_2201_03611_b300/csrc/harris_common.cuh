@@ -35,6 +35,11 @@ constexpr float kGrayR = 0.299f, kGrayG = 0.587f, kGrayB = 0.114f;
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
+// A1 for one pixel.
+__device__ __forceinline__ float gray_of(float r, float g, float b) {
+    return fmaf(kGrayB, b, fmaf(kGrayG, g, kGrayR * r));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Storage types: float32 arithmetic, float32 / bf16 / fp16 storage (round to nearest even).
 // ---------------------------------------------------------------------------------------------
@@ -62,6 +67,35 @@ template <> struct Bits16<__half> {
         return __half2float(__ushort_as_half((unsigned short)b16));
     }
 };
+
+// 16-bit channel values unpacked from a word holding two of them (element 0 in the low half).
+__device__ __forceinline__ uint32_t lo16_to_hi(uint32_t w) {  // low half moved up, low half zero
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, 0x1044;" : "=r"(d) : "r"(w));
+    return d;
+}
+template <typename T> struct Unpack16;
+template <> struct Unpack16<__nv_bfloat16> {
+    __device__ __forceinline__ static float lo(uint32_t w) { return __uint_as_float(lo16_to_hi(w)); }
+    __device__ __forceinline__ static float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+};
+template <> struct Unpack16<__half> {
+    __device__ __forceinline__ static float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    __device__ __forceinline__ static float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+};
+
+// Gray values of two adjacent 16-bit pixels from their three words (pixel 0: r, g in w0, b in the
+// low half of w1; pixel 1: r in the high half of w1, g, b in w2), unpacked straight into the
+// (pixel 0, pixel 1) pair of each channel and weighed with packed multiply-adds; each half is the
+// scalar chain fma(kB, b, fma(kG, g, kR * r)) of gray_of.
+template <typename T>
+__device__ __forceinline__ float2 gray2_16(uint32_t w0, uint32_t w1, uint32_t w2) {
+    const float2 r = make_float2(Unpack16<T>::lo(w0), Unpack16<T>::hi(w1));
+    const float2 g = make_float2(Unpack16<T>::hi(w0), Unpack16<T>::lo(w2));
+    const float2 b = make_float2(Unpack16<T>::lo(w1), Unpack16<T>::hi(w2));
+    return __ffma2_rn(make_float2(kGrayB, kGrayB), b,
+                      __ffma2_rn(make_float2(kGrayG, kGrayG), g, __fmul2_rn(make_float2(kGrayR, kGrayR), r)));
+}
 
 // ---------------------------------------------------------------------------------------------
 // cp.async (LDGSTS) helpers. src_bytes < cp-size zero-fills the rest of the chunk and reads
@@ -360,9 +394,6 @@ __device__ __forceinline__ void clamp_row6(V r6[6], int x, int W) {
         if (x - 1 + p == W) r6[p] = r6[p - 1];
 }
 
-__device__ __forceinline__ float gray_of(float r, float g, float b) {
-    return fmaf(kGrayB, b, fmaf(kGrayG, g, kGrayR * r));
-}
 
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 

@@ -134,33 +134,13 @@ __device__ __forceinline__ void wide_add_S(WideRun& st) {
 // time straight into the (pixel j, pixel j+1) pairs of each channel and weighed with packed
 // multiply-adds; each half is the scalar chain fma(kB, b, fma(kG, g, kR * r)) of gray_of.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t lo16_to_hi(uint32_t w) {  // low half moved up, low half zero
-    uint32_t d;
-    asm("prmt.b32 %0, %1, 0, 0x1044;" : "=r"(d) : "r"(w));
-    return d;
-}
-template <typename T> struct Unpack16;
-template <> struct Unpack16<__nv_bfloat16> {
-    __device__ __forceinline__ static float lo(uint32_t w) { return __uint_as_float(lo16_to_hi(w)); }
-    __device__ __forceinline__ static float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-};
-template <> struct Unpack16<__half> {
-    __device__ __forceinline__ static float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
-    __device__ __forceinline__ static float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-};
-
-// 16-bit: q[0..5] are the 12 words of 24 channel values (pixel 2i in words 3i, 3i+1 low half;
+// 16-bit: w[0..11] are the 12 words of 24 channel values (pixel 2i in words 3i, 3i+1 low half;
 // pixel 2i+1 in words 3i+1 high half, 3i+2).
 template <typename T>
 __device__ __forceinline__ void gray8_16(const uint32_t w[12], float c[8]) {
-    const float2 kr = dup2(kGrayR), kg = dup2(kGrayG), kb = dup2(kGrayB);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const uint32_t w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
-        const float2 r = make_float2(Unpack16<T>::lo(w0), Unpack16<T>::hi(w1));
-        const float2 g = make_float2(Unpack16<T>::hi(w0), Unpack16<T>::lo(w2));
-        const float2 b = make_float2(Unpack16<T>::lo(w1), Unpack16<T>::hi(w2));
-        const float2 y = __ffma2_rn(kb, b, __ffma2_rn(kg, g, __fmul2_rn(kr, r)));
+        const float2 y = gray2_16<T>(w[3 * i], w[3 * i + 1], w[3 * i + 2]);
         c[2 * i] = y.x;
         c[2 * i + 1] = y.y;
     }
