@@ -633,15 +633,16 @@ def mv_extra(S, device, n: int, reps: int) -> dict:
 
 
 def batched_extra(S, device, n: int, reps: int) -> dict:
-    """The uneven batch: n images, bf16 storage, forward + backward fused in one persistent
-    launch captured in a CUDA graph, against a loop of per-image fused launches."""
-    b = wl.batch_512(n=n)
-    imgs = [t.to(device) for t in b["imgs"]]
-    gouts = [t.to(device) for t in b["ws"]]
+    """The uneven batch: n images, bf16 storage with every row pitch rounded up to 16 bytes,
+    forward + backward fused in one persistent launch captured in a CUDA graph, against a loop
+    of per-image fused launches on the same buffers."""
+    b = wl.batch_512(n=n)  # row pitches rounded up to 16 bytes
+    imgs = [wl.to_device(t, device) for t in b["imgs"]]
+    gouts = [wl.to_device(t, device) for t in b["ws"]]
     shapes = [tuple(t.shape[:2]) for t in imgs]
     px = sum(h * w for h, w in shapes)
-    outs = [torch.empty(h, w, dtype=imgs[0].dtype, device=device) for h, w in shapes]
-    gimgs = [torch.empty_like(t) for t in imgs]
+    outs = [wl.empty_padded((h, w), imgs[0].dtype, device) for h, w in shapes]
+    gimgs = [wl.empty_padded((h, w, 3), imgs[0].dtype, device) for h, w in shapes]
     kappa = b["kappa"].to(device)
     wx, wy = [t.to(device) for t in wl.sobel_weights()]
     cache = os.path.join(ROOT, "paper_2201_03611_b300", "tune_cache.txt")

@@ -105,11 +105,11 @@ def main():
     ap.add_argument("--fwd-only", action="store_true")
     args = ap.parse_args()
     b = wl.batch_512(n=args.n, dtype=args.dtype)
-    imgs = [t.cuda() for t in b["imgs"]]
-    gouts = [t.cuda() for t in b["ws"]]
+    imgs = [wl.to_device(t, "cuda") for t in b["imgs"]]
+    gouts = [wl.to_device(t, "cuda") for t in b["ws"]]
     shapes = [tuple(t.shape[:2]) for t in imgs]
-    outs = [torch.empty(h, w, dtype=imgs[0].dtype, device="cuda") for h, w in shapes]
-    gimgs = [torch.empty_like(t) for t in imgs]
+    outs = [wl.empty_padded((h, w), imgs[0].dtype, "cuda") for h, w in shapes]
+    gimgs = [wl.empty_padded((h, w, 3), imgs[0].dtype, "cuda") for h, w in shapes]
     wx, wy = [t.cuda() for t in wl.sobel_weights()]
     table = tune(shapes, imgs, outs, None if args.fwd_only else gouts, None if args.fwd_only else gimgs,
                  b["kappa"].cuda(), wx, wy, imgs[0].dtype, "clamp", not args.fwd_only, args.out, verbose=True)

@@ -19,10 +19,10 @@ def shine():
     return S
 
 
-def _batch(n, dtype, seed, lo=5, hi=300, border="clamp"):
-    b = wl.batch_512(n=n, dtype=dtype, seed=seed, lo=lo, hi=hi)
-    imgs = [t.cuda() for t in b["imgs"]]
-    ws = [t.cuda() for t in b["ws"]]
+def _batch(n, dtype, seed, lo=5, hi=300, border="clamp", pad16=True):
+    b = wl.batch_512(n=n, dtype=dtype, seed=seed, lo=lo, hi=hi, pad16=pad16)
+    imgs = [wl.to_device(t, "cuda") for t in b["imgs"]]
+    ws = [wl.to_device(t, "cuda") for t in b["ws"]]
     if border == "valid":
         ws = [w[: w.shape[0] - 4, : w.shape[1] - 4].contiguous() for w in ws]
     return b, imgs, ws
@@ -30,8 +30,9 @@ def _batch(n, dtype, seed, lo=5, hi=300, border="clamp"):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("border", ["clamp", "valid"])
-def test_batched_equals_per_image(shine, dtype, border):
-    b, imgs, ws = _batch(14, dtype, seed=3, border=border)
+@pytest.mark.parametrize("pad16", [True, False])
+def test_batched_equals_per_image(shine, dtype, border, pad16):
+    b, imgs, ws = _batch(14, dtype, seed=3, border=border, pad16=pad16)
     shapes = [tuple(t.shape[:2]) for t in imgs]
     plan = shine.BatchedPlan(shapes, imgs[0].dtype, border, fwd_bwd=True)
     outs = [torch.empty(shine.output_shape(h, w, border), dtype=imgs[0].dtype, device="cuda") for h, w in shapes]
@@ -149,7 +150,8 @@ def test_tune_cache_is_honoured(shine, tmp_path):
 
 def test_batched_512_workload_with_tuned_tiles(shine):
     """The benchmark's own uneven batch in the benchmark's launch configuration: the 512 bf16
-    images (sizes log-uniform in [64, 2048], seed 2), the committed tuning cache (tall bands of
+    images (sizes log-uniform in [64, 2048], seed 2, row pitches rounded up to 16 bytes, outputs
+    likewise), the committed tuning cache (tall bands of
     512 and 1024 rows on the large images, so multi-band images occur), one persistent launch
     replayed from a CUDA graph. Every image's R, d img and d kappa_i against the FP64 oracle on
     the quantised input, d Wx and d Wy against the oracle's sums over the batch, and R and d img
@@ -158,8 +160,8 @@ def test_batched_512_workload_with_tuned_tiles(shine):
                          "tune_cache.txt")
     b = wl.batch_512()
     n = len(b["imgs"])
-    imgs = [t.cuda() for t in b["imgs"]]
-    gouts = [t.cuda() for t in b["ws"]]
+    imgs = [wl.to_device(t, "cuda") for t in b["imgs"]]
+    gouts = [wl.to_device(t, "cuda") for t in b["ws"]]
     shapes = [tuple(t.shape[:2]) for t in imgs]
     plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=cache)
     default = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True)
@@ -167,8 +169,8 @@ def test_batched_512_workload_with_tuned_tiles(shine):
     assert rows != [default.tile_rows(i) for i in range(n)], "tuning cache not picked up on this GPU"
     big = [i for i, (h, _) in enumerate(shapes) if h >= 1024]
     assert big and any(shapes[i][0] > rows[i] for i in big), "no multi-band image in the batch"
-    outs = [torch.empty(h, w, dtype=torch.bfloat16, device="cuda") for h, w in shapes]
-    gimgs = [torch.empty_like(t) for t in imgs]
+    outs = [wl.empty_padded((h, w), torch.bfloat16, "cuda") for h, w in shapes]
+    gimgs = [wl.empty_padded((h, w, 3), torch.bfloat16, "cuda") for h, w in shapes]
     descs = plan.bind(imgs, outs, gouts, gimgs)
     ws_buf = plan.new_workspace("cuda")
     kappa = b["kappa"].cuda()

@@ -17,7 +17,8 @@ Workloads (images are H x W x 3, HWC interleaved, channel fastest):
                     ``w = randn(8192,8192)`` seed 1 cast the same way.
 * ``batch_512``     seed 2: sizes ``round(exp(U(ln 64, ln 2048)))`` as a (512, 2) draw,
                     kappa_i ~ U(0.02, 0.08), then per image ``rand(H,W,3)`` and
-                    ``randn(H,W)`` in order from the same generator; bf16 storage.
+                    ``randn(H,W)`` in order from the same generator; bf16 storage, every
+                    row pitch (image and cotangent) rounded up to a multiple of 16 bytes.
 """
 from __future__ import annotations
 
@@ -112,14 +113,52 @@ def batch_sizes(n: int = 512, seed: int = 2, lo: int = 64, hi: int = 2048):
     return hw, kappa.to(torch.float32), g
 
 
-def batch_512(n: int = 512, dtype: str = "bf16", seed: int = 2, lo: int = 64, hi: int = 2048) -> dict:
-    """The uneven batch: per-image images and cotangents drawn in order after the sizes."""
+def padded(t: torch.Tensor, row_bytes: int = 16) -> torch.Tensor:
+    """The same values with every row (first dimension) padded to a multiple of row_bytes bytes:
+    a strided view into a zero-filled buffer of whole padded rows."""
+    h = t.shape[0]
+    row = t.reshape(h, -1)
+    esize = t.element_size()
+    pitch = -(-row.shape[1] * esize // row_bytes) * row_bytes // esize
+    store = torch.zeros(h, pitch, dtype=t.dtype, device=t.device)
+    store[:, :row.shape[1]] = row
+    strides = (pitch,) + tuple(t.stride()[1:])
+    return store.as_strided(t.shape, strides)
+
+
+def to_device(t: torch.Tensor, device) -> torch.Tensor:
+    """Copy of a (possibly row-padded) tensor on `device` with the same strides."""
+    h, pitch = t.shape[0], t.stride(0)
+    return torch.as_strided(t, (h, pitch), (pitch, 1)).to(device).as_strided(t.shape, t.stride())
+
+
+def empty_padded(shape, dtype: torch.dtype, device, row_bytes: int = 16) -> torch.Tensor:
+    """An uninitialised tensor of `shape` whose rows are padded to a multiple of row_bytes bytes."""
+    esize = torch.empty(0, dtype=dtype).element_size()
+    row = 1
+    for d in shape[1:]:
+        row *= d
+    pitch = -(-row * esize // row_bytes) * row_bytes // esize
+    store = torch.empty(shape[0], pitch, dtype=dtype, device=device)
+    strides, acc = [], 1
+    for d in reversed(shape[1:]):
+        strides.insert(0, acc)
+        acc *= d
+    return store.as_strided(tuple(shape), (pitch,) + tuple(strides))
+
+
+def batch_512(n: int = 512, dtype: str = "bf16", seed: int = 2, lo: int = 64, hi: int = 2048,
+              pad16: bool = True) -> dict:
+    """The uneven batch: per-image images and cotangents drawn in order after the sizes; with
+    pad16 every row pitch is rounded up to a multiple of 16 bytes (see padded, to_device)."""
     hw, kappa, g = batch_sizes(n, seed, lo, hi)
     imgs, ws = [], []
     for i in range(n):
         h, w = int(hw[i, 0]), int(hw[i, 1])
-        imgs.append(torch.rand(h, w, 3, generator=g, dtype=torch.float32).to(_DTYPES[dtype]))
-        ws.append(torch.randn(h, w, generator=g, dtype=torch.float32).to(_DTYPES[dtype]))
+        img = torch.rand(h, w, 3, generator=g, dtype=torch.float32).to(_DTYPES[dtype])
+        wi = torch.randn(h, w, generator=g, dtype=torch.float32).to(_DTYPES[dtype])
+        imgs.append(padded(img) if pad16 else img)
+        ws.append(padded(wi) if pad16 else wi)
     return {"hw": hw, "kappa": kappa, "imgs": imgs, "ws": ws, "border": "clamp"}
 
 
