@@ -182,8 +182,10 @@ SHINE_API shine_status shine_pipeline_bwd_noalloc(const void* img, int64_t H, in
  *
  * shine_plan_create builds, on the host and then once on the device, the tile list of a fixed
  * set of image shapes (HW: host array of n (H, W) pairs), choosing the tile height per shape
- * bucket (from tune_cache_path when given and it holds an entry for this GPU, else a built-in
- * rule). mode: SHINE_MODE_FWD computes R only; SHINE_MODE_FWD_BWD also computes the
+ * bucket and the schedule (see shine_plan_schedule) from tune_cache_path when given and it holds
+ * entries for this GPU, else built-in rules. Cache lines (text, '#' comments):
+ *   <gpu key> <dtype> <border> <mode> <bucket> <band_rows>      bucket = ceil(log2(rows))
+ *   <gpu key> <dtype> <border> <mode> plan <order> <staging> <edge_w4> <origin> mode: SHINE_MODE_FWD computes R only; SHINE_MODE_FWD_BWD also computes the
  * cotangents of L = sum_i sum(grad_out_i * R_i) in the same pass (grad_out is an input given
  * up front). This is the only call that allocates (host memory and one device buffer).
  */
@@ -209,12 +211,29 @@ SHINE_API shine_status shine_plan_workspace(const shine_plan* plan, size_t* byte
 SHINE_API shine_status shine_plan_tile_rows(const shine_plan* plan, int32_t i, int32_t* rows);
 
 /*
+ * The schedule the plan chose (host; no counterpart in the paper): the order in which the
+ * persistent warps claim the tiles (SHINE_ORDER_*: longest tile first, image by image, or the
+ * images with the most work first), the staging of interior segments in SHINE_MODE_FWD_BWD
+ * (0: every lane copies its own chunks with cp.async; 1: bulk copies by one lane, for images
+ * whose image and cotangent rows are 16-byte aligned), the weight of an edge-segment tile row
+ * against an interior one (edge_w4 / 4) in the claim order's work estimate, and the first output
+ * column of segment 0 of every image (segments are 120 columns wide). All four come from the
+ * tuning cache's "plan" line when it has one for this GPU, else from the defaults (longest
+ * first, cp.async, 6, 0).
+ */
+enum { SHINE_ORDER_LONGEST_FIRST = 0, SHINE_ORDER_IMAGE = 1, SHINE_ORDER_LARGEST_IMAGE_FIRST = 2 };
+SHINE_API shine_status shine_plan_schedule(const shine_plan* plan, int32_t* order, int32_t* staging,
+                                           int32_t* edge_w4, int32_t* origin);
+
+/*
  * Run the plan: descs is a DEVICE array of n image descriptors (same order and shapes as at
  * plan creation), kappa [n] one per image, wx/wy [9] shared by every image. grad_kappa [n],
  * grad_wx [9], grad_wy [9] are float32 outputs (nullable; FWD_BWD mode). Launches a
  * persistent kernel (one CTA per SM slot, tiles claimed from an atomic counter in the
  * workspace) and a fixed-order reduction; no allocation and no synchronisation, so the call
- * can be captured in a CUDA graph. Results do not depend on which CTA ran which tile.
+ * can be captured in a CUDA graph. Results do not depend on which CTA ran which tile. A bounded
+ * wait of bulk staging that gives up (results invalid) sets the workspace's first word, which
+ * shine_workspace_status reads.
  */
 SHINE_API shine_status shine_pipeline_batched(const shine_plan* plan, const shine_image_desc* descs,
                                     const float* kappa, const float* wx, const float* wy,

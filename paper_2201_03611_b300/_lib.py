@@ -16,6 +16,7 @@ SHINE_OK, SHINE_ERR_INVALID_ARG, SHINE_ERR_ALIGNMENT, SHINE_ERR_WORKSPACE, SHINE
 SHINE_F32, SHINE_BF16, SHINE_F16 = 0, 1, 2
 SHINE_VALID, SHINE_CLAMP = 0, 1
 SHINE_MODE_FWD, SHINE_MODE_FWD_BWD = 1, 3
+SHINE_ORDER_LONGEST_FIRST, SHINE_ORDER_IMAGE, SHINE_ORDER_LARGEST_IMAGE_FIRST = 0, 1, 2
 
 
 class ShineError(RuntimeError):
@@ -71,6 +72,8 @@ def lib() -> ctypes.CDLL:
         "shine_plan_create": (st, [ctypes.POINTER(i64), i32, f, f, i32, ctypes.c_char_p, ctypes.POINTER(p)]),
         "shine_plan_workspace": (st, [p, ctypes.POINTER(sz)]),
         "shine_plan_tile_rows": (st, [p, i32, ctypes.POINTER(i32)]),
+        "shine_plan_schedule": (st, [p, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32)]),
         "shine_pipeline_batched": (st, [p, p, p, p, p, p, p, p, p, sz, p]),
         "shine_plan_destroy": (None, [p]),
         "shine_status_string": (ctypes.c_char_p, [f]),

@@ -39,6 +39,12 @@ class BatchedPlan:
         L.check(L.lib().shine_plan_tile_rows(self._h, i, ctypes.byref(r)), "shine_plan_tile_rows")
         return r.value
 
+    def schedule(self) -> dict:
+        """The schedule the plan chose (claim order, staging, edge weight x 4, segment origin)."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        L.check(L.lib().shine_plan_schedule(self._h, *[ctypes.byref(x) for x in v]), "shine_plan_schedule")
+        return dict(zip(("order", "staging", "edge_w4", "origin"), (x.value for x in v)))
+
     def bind(self, imgs, outs=None, grad_outs=None, grad_imgs=None) -> torch.Tensor:
         """Device array of shine_image_desc for these tensors (kept alive by the caller)."""
         if len(imgs) != self.n:

@@ -143,9 +143,69 @@ def test_tune_cache_is_honoured(shine, tmp_path):
     shapes = [(100, 90), (1000, 40), (33, 33)]
     path = tmp_path / "tune.txt"
     # bucket of 100 rows is 7 (2^7 = 128 >= 100), of 1000 rows 10, of 33 rows 6
-    path.write_text(f"# test\n{gpu_key()} 1 1 3 7 24\n{gpu_key()} 1 1 3 10 200\n")
+    path.write_text(f"# test\n{gpu_key()} 1 1 3 7 24\n{gpu_key()} 1 1 3 10 200\n"
+                    f"{gpu_key()} 1 1 3 plan 2 1 10 -28\n")
     plan = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=str(path))
     assert [plan.tile_rows(i) for i in range(3)] == [24, 200, 33]
+    assert plan.schedule() == {"order": 2, "staging": 1, "edge_w4": 10, "origin": -28}
+    default = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True)
+    assert default.schedule() == {"order": 0, "staging": 0, "edge_w4": 6, "origin": 0}
+    # a schedule the kernels cannot run (bulk-staged 16-bit spans need origin = 4 mod 8) is ignored
+    path.write_text(f"{gpu_key()} 1 1 3 plan 1 1 6 0\n")
+    bad = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=str(path))
+    assert bad.schedule() == default.schedule()
+    # another mode's plan line does not apply
+    path.write_text(f"{gpu_key()} 1 1 1 plan 1 0 8 -4\n")
+    other = shine.BatchedPlan(shapes, torch.bfloat16, "clamp", fwd_bwd=True, tune_cache=str(path))
+    assert other.schedule() == default.schedule()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_schedules_give_the_same_results(shine, tmp_path, dtype):
+    """Every schedule the tuner can choose (claim order, staging of interior segments, edge
+    weight, segment origin, band heights) computes the same R and d img bit for bit -- the
+    per-pixel arithmetic does not depend on the tiling -- and parameter cotangents within the
+    summation tolerance of the oracle's."""
+    from paper_2201_03611_b300.tune import gpu_key
+    b, imgs, ws = _batch(10, dtype, seed=13, lo=40, hi=700)
+    shapes = [tuple(t.shape[:2]) for t in imgs]
+    kappa = b["kappa"].cuda()
+    wx, wy = [t.cuda() for t in wl.random_weights(21)]
+    refs = [cref.backward(b["imgs"][i], b["ws"][i], float(b["kappa"][i]), wx.cpu(), wy.cpu(), "clamp", with_abs=True)
+            for i in range(len(imgs))]
+    swx = sum(r[2] for r in refs)
+    swy = sum(r[3] for r in refs)
+    awx = sum(r[4][1] for r in refs)
+    awy = sum(r[4][2] for r in refs)
+    dt = 0 if dtype == "f32" else 1
+    first = None
+    for order, staging, ew4, origin, rows in ((0, 0, 6, 0, 0), (1, 1, 8, -4, 64), (2, 1, 4, -76, 32),
+                                               (0, 0, 12, -28, 128), (2, 0, 5, -100, 16)):
+        path = tmp_path / "tune.txt"
+        lines = [f"{gpu_key()} {dt} 1 3 plan {order} {staging} {ew4} {origin}"]
+        if rows:
+            lines += [f"{gpu_key()} {dt} 1 3 {bk} {rows}" for bk in range(12)]
+        path.write_text("\n".join(lines) + "\n")
+        plan = shine.BatchedPlan(shapes, imgs[0].dtype, "clamp", fwd_bwd=True, tune_cache=str(path))
+        assert plan.schedule() == {"order": order, "staging": staging, "edge_w4": ew4, "origin": origin}
+        outs = [wl.empty_padded((h, w), imgs[0].dtype, "cuda") for h, w in shapes]
+        gimgs = [wl.empty_padded((h, w, 3), imgs[0].dtype, "cuda") for h, w in shapes]
+        descs = plan.bind(imgs, outs, ws, gimgs)
+        ws_buf = plan.new_workspace("cuda")
+        gk = torch.empty(len(imgs), device="cuda")
+        gwx, gwy = torch.empty(3, 3, device="cuda"), torch.empty(3, 3, device="cuda")
+        plan.run(descs, kappa, wx, wy, gk, gwx, gwy, ws_buf)
+        torch.cuda.synchronize()
+        assert not shine.ops.workspace_failed(ws_buf)
+        got = [t.clone() for t in outs + gimgs]
+        if first is None:
+            first = got
+        else:
+            assert all(torch.equal(x, y) for x, y in zip(first, got)), (order, staging, ew4, origin, rows)
+        for i in range(len(imgs)):
+            assert abs(float(gk[i]) - refs[i][1]) <= U.TOL_PARAM_COND * refs[i][4][0]
+        U.assert_params((gk[:1], gwx, gwy), (float(U.host(gk[:1])[0]), swx, swy, (1.0, awx, awy)))
+        plan.close()
 
 
 def test_batched_512_workload_with_tuned_tiles(shine):
