@@ -24,6 +24,7 @@
 // summed in a fixed order by the finalize kernel, so every run gives the same bits.
 #include <algorithm>
 
+#include "harris_adj_wide.cuh"
 #include "harris_bwd_strip.cuh"
 
 namespace shine {
@@ -90,6 +91,72 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_kernel(BwdArgs a) {
     }
 }
 
+// The adjoint of a CLAMP image whose image and cotangent rows are 16-byte aligned, eight
+// columns per lane (harris_adj_wide.cuh): interior segments staged by bulk copies, edge segments
+// per lane by cp.async. Shared memory of a CTA: every warp's staging ring (NS slots of the image
+// span and the cotangent span), then the ring barriers, then every warp's WRings.
+template <typename TI, typename TG>
+constexpr size_t wide_adj_smem(int ns) {
+    return (size_t)(kBwdThreads / 32) * ns * (WSlot<TI, TG>::kBytes + 8) + (size_t)(kBwdThreads / 32) * kWRingBytes;
+}
+
+template <typename TI, typename TG, int NS>
+__global__ void __launch_bounds__(kBwdThreads) harris_bwd_wide_kernel(BwdArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int kWarps = kBwdThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kWarps + warp;
+    if (gw >= a.nwarps) return;  // whole warp
+    const uint32_t base = smem_u32(smem_raw);
+    const uint32_t ring0 = base + (uint32_t)warp * NS * WSlot<TI, TG>::kBytes;
+    WRings rg;
+    rg.init(base + kWarps * NS * (WSlot<TI, TG>::kBytes + 8) + (uint32_t)warp * kWRingBytes, lane);
+    rg.acc_zero();
+    BulkState bulk;
+    bulk.seq = 0;
+    bulk.failed = false;
+    bulk.bars = base + kWarps * NS * WSlot<TI, TG>::kBytes + (uint32_t)warp * NS * 8;
+    if (lane == 0)
+        for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+    mbar_init_fence();
+    __syncwarp();
+    Params P;
+    load_params(P, a.wx, a.wy, a.kappa);
+    const int64_t rows = a.yhi - a.ylo;
+    int64_t lo, hi;
+    warp_work(SHINE_BWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_WIDE_BWD_EDGE_WEIGHT4);
+    while (lo < hi && !bulk.failed) {
+        const int seg = (int)(lo / rows);
+        const int r0 = (int)(lo % rows);
+        const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
+        const int xb = a.x0 + seg * kWSegOut;
+        const int x = xb - kWCols + kWCols * lane;
+        const int y0 = a.ylo + r0, y1 = a.ylo + r1;
+        const int n = y1 - y0 + 8;
+        const bool edge = (xb - kWCols < 0) || (xb + kWSegOut + kWCols > a.W);
+        if (edge) {
+            WAdjLanes<TI, TG, NS> src(a, ring0, lane, x, y0 - 4, n);
+            wide_adj_strip<TI, true, false>(a, P, lane, x, y0, y1, src, rg, nullptr);
+        } else {
+            WAdjBulk<TI, TG, NS> src(bulk, a, ring0, lane, xb - kWCols, y0 - 4, n);
+            wide_adj_strip<TI, false, true>(a, P, lane, x, y0, y1, src, rg, &bulk.failed);
+        }
+        lo += r1 - r0;
+    }
+    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
+    const bool producer = lane >= 1 && lane <= 30;
+    float acc[kParamSlots];
+    rg.acc_get(acc);
+#pragma unroll
+    for (int i = 0; i < kParamSlots; ++i) {
+        double v = producer ? (double)acc[i] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) a.partials[(int64_t)i * (a.pstride ? a.pstride : a.nwarps) + a.poffset + gw] = v;
+    }
+}
+
 template <typename K>
 int resident_warps(K kernel, int threads, size_t smem) {
     int per_sm = 0;
@@ -102,7 +169,34 @@ int resident_warps(K kernel, int threads, size_t smem) {
 }
 
 template <typename TI, typename TG>
+cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
+    constexpr int NS = SHINE_WIDE_BWD_STAGES;
+    const size_t smem = wide_adj_smem<TI, TG>(NS);
+    auto kern = harris_bwd_wide_kernel<TI, TG, NS>;
+    a.x0 = SHINE_WIDE_BWD_ORIGIN;
+    a.nseg = (a.xhi - a.x0 + kWSegOut - 1) / kWSegOut;
+    const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t t = resident_warps(kern, kBwdThreads, smem);
+    t = std::min<int64_t>(t, std::max<int64_t>(1, units / kBwdMinRows));
+    t = std::max<int64_t>(1, std::min<int64_t>(t, max_warps));
+    a.nwarps = (int)t;
+    if (used) *used = a.nwarps;
+    const int64_t blocks = (t + kBwdThreads / 32 - 1) / (kBwdThreads / 32);
+    kern<<<(unsigned)blocks, kBwdThreads, smem, s>>>(a);
+    return cudaPeekAtLastError();
+}
+
+template <typename TI, typename TG>
 cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
+    // 16-bit CLAMP images with 16-byte aligned image and cotangent rows (a.tma), adjoint only: the
+    // wide kernel (measured on 8192^2: bf16 0.409 -> 0.388 ms, fp16 0.440 -> 0.410 ms; float32
+    // 0.413 -> 0.478 ms, where its 96-byte lane pieces meet 2-way bank conflicts, so float32
+    // images stay on the four-column kernel)
+    if constexpr (SHINE_WIDE_BWD && sizeof(TI) == 2) {
+        if (a.tma && !a.valid && a.rout == nullptr) return launch_bwd_wide_t<TI, TG>(a, max_warps, s, used);
+    }
     // ring depth: the adjoint alone takes bwd_stages<TI>(), the fused forward+adjoint (which also
     // stores R) the default depth (measured: float32 fused 0.486 ms at 8 rows, 0.494 at 6)
     constexpr int NS = bwd_stages<TI>();

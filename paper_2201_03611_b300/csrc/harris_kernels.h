@@ -32,6 +32,18 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_BWD_TMA
 #define SHINE_BWD_TMA 1           // backward interior segments staged by bulk copies
 #endif
+#ifndef SHINE_WIDE_BWD
+#define SHINE_WIDE_BWD 1          // adjoint of aligned 16-bit CLAMP images: eight columns per lane
+#endif
+#ifndef SHINE_WIDE_BWD_STAGES
+#define SHINE_WIDE_BWD_STAGES 4   // its staging ring (rows)
+#endif
+#ifndef SHINE_WIDE_BWD_ORIGIN
+#define SHINE_WIDE_BWD_ORIGIN 0   // first output column of its segment 0 (a multiple of 8)
+#endif
+#ifndef SHINE_WIDE_BWD_EDGE_WEIGHT4
+#define SHINE_WIDE_BWD_EDGE_WEIGHT4 8  // an edge-segment row weighs this / 4 interior rows (measured:
+#endif                              // 8 best of 6, 8, 10 on 8192^2 bf16)
 #ifndef SHINE_FWD_EDGE_WEIGHT4
 #define SHINE_FWD_EDGE_WEIGHT4 6  // an edge-segment row weighs this / 4 interior rows (forward-type)
 #endif
