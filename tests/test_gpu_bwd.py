@@ -223,3 +223,26 @@ def test_host_pipeline_matches_device_calls(shine, shape, border, dtype, nbands)
     assert torch.equal(gimg_h, gi.cpu())
     ref = cref.backward(img_h, g_h, 0.05, wx.cpu(), wy.cpu(), border, with_abs=True)
     U.assert_params((par[0:1], par[1:10].reshape(3, 3), par[10:19].reshape(3, 3)), ref[1:])
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("shape", [(1, 8), (3, 16), (9, 248), (37, 256), (64, 496), (130, 512), (300, 264),
+                                   (5, 1024), (257, 744)])
+def test_bwd_16bit_wide_path(shine, dtype, shape):
+    """16-bit CLAMP images whose rows are 16-byte aligned (W a multiple of 8) take the eight-
+    columns-per-lane adjoint: interior segments bulk-staged, edge segments staged per lane, ragged
+    column and row tails. d img must equal, bit for bit, the four-column adjoint's (reached through
+    an unaligned row pitch, same arithmetic per pixel), and everything must match the oracle on the
+    quantised input."""
+    h, w = shape
+    img = wl.random_image(h, w, seed=h + w).to(dtype).cuda()
+    g = wl.random_cotangent(h, w, seed=h * w).to(dtype).cuda()
+    wx, wy = wl.random_weights(h)
+    k, dwx, dwy = U.dev_params(0.05, wx, wy)
+    wide = shine.pipeline_bwd(img, g, k, dwx, dwy, "clamp")
+    narrow = shine.pipeline_bwd(U.padded_image(img, 1), g, k, dwx, dwy, "clamp")
+    torch.cuda.synchronize()
+    assert torch.equal(wide[0], narrow[0])
+    ref = cref.backward(img.cpu(), g.cpu(), 0.05, wx, wy, "clamp", with_abs=True)
+    assert U.rel(U.host(wide[0]), ref[0]) <= U.TOL_16
+    U.assert_params(wide[1:], ref[1:])
