@@ -392,10 +392,11 @@ def precision_extra(S, device, size: int, reps: int) -> dict:
 
 def small_configs_extra(S, device, reps: int) -> dict:
     """The two workloads smaller than L2, each launch timed alone with L2 flushed before it
-    (a 256 MB write): the 256 x 256 VALID forward (latency-bound: a parity workload, its time is
+    (a 256 MB write, then a read of the same buffer): the 256 x 256 VALID forward (latency-bound: a parity workload, its time is
     reported, not held to the roofline) and the 2048 x 2048 differentiation workload's forward
     and backward passes (loss sum(w * R), w ~ N(0, 1) from seed 1)."""
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    sink = torch.empty(1, dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream(device)
     wx, wy = wl.sobel_weights()
     k = torch.tensor([wl.KAPPA], device=device)
@@ -406,7 +407,11 @@ def small_configs_extra(S, device, reps: int) -> dict:
             fn()
         ts = []
         for _ in range(reps):
+            # flush: write 256 MB (twice the L2), then read it back, so that the lines the timed
+            # launch finds in L2 are clean ones of the flush buffer, not dirty ones whose
+            # write-back it would pay for
             flush.zero_()
+            torch.sum(flush, dim=0, keepdim=True, out=sink)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()

@@ -218,8 +218,14 @@ cudaError_t launch_harris_bwd(BwdArgs a, int dt, int gout_dt, int max_warps, cud
 // Minimum rows per warp slice when an image has fewer (segment, row) units than resident warps:
 // small images take more, shorter slices (measured, L2 flushed: 512^2 forward 16.4 -> 10.2 us,
 // adjoint 54 -> 34 us; 1024^2 adjoint 52 -> 40 us; 8192^2 unchanged).
-constexpr int kFwdMinRows = 2;
-constexpr int kBwdMinRows = 4;
+#ifndef SHINE_FWD_MIN_ROWS
+#define SHINE_FWD_MIN_ROWS 2
+#endif
+#ifndef SHINE_BWD_MIN_ROWS
+#define SHINE_BWD_MIN_ROWS 4
+#endif
+constexpr int kFwdMinRows = SHINE_FWD_MIN_ROWS;
+constexpr int kBwdMinRows = SHINE_BWD_MIN_ROWS;
 constexpr int kMaxWarpsPerSm = 64;
 constexpr size_t kWorkspaceHeader = 256;  // backward workspace: error word, then the partial sums
 // First output column of segment 0 in the single-image kernels, per pass. Any origin = 4
