@@ -354,9 +354,32 @@ def _time_ms(fn, reps: int, stream) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+# Float32 pipe work per output pixel of the two passes, in FMA-pipe lane cycles (a fused or plain
+# float32 multiply or add 1, a packed float32x2 one 2), counted from the arithmetic each pass must
+# do (32/30 for the halo lanes included): forward = gray 3 + Sobel (2 planes x 9 taps) 18 +
+# products 9 + box sums 6 + response 5; adjoint = the recompute of gray, Sobel, products and box
+# sums 36 + gS and the d kappa terms 11 + box adjoint 12 + B4 6 + weight cotangent 18 +
+# transposed stencil 18 + d img 4.
+FMA_LANE_CYCLES_PER_PX = {"fwd": 41 * 32 / 30, "bwd": 105 * 32 / 30}
+
+
+def _fma_lane_cycles_per_s() -> float:
+    """FMA-pipe peak of the device: SMs x 128 float32 lanes x maximum SM clock."""
+    props = torch.cuda.get_device_properties(0)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2032.0
+    return props.multi_processor_count * 128 * mhz * 1e6
+
+
 def precision_extra(S, device, size: int, reps: int) -> dict:
     """The precision workload: bf16 / fp16 storage (float32 arithmetic), forward + backward of the
-    unsalted size x size image, timed like the main step. Its errors against the oracle (on the
+    unsalted size x size image, timed like the main step. Besides the fraction of the HBM copy
+    rate, each pass reports the fraction of the float32 pipe's peak its arithmetic needs (16-bit
+    storage halves the bytes, not the arithmetic, so these passes are bound by the FMA pipe and
+    instruction issue). Its errors against the oracle (on the
     quantised and on the float32 input) are measured by tests/test_gpu_precision.py, which
     prints them; the benchmark itself runs no oracle code outside the CPU-baseline leg."""
     out = {}
@@ -381,10 +404,13 @@ def precision_extra(S, device, size: int, reps: int) -> dict:
         t_f = _time_ms(fwd, reps, stream)
         t_b = _time_ms(bwd, reps, stream)
         px = size * size
+        fma_peak = _fma_lane_cycles_per_s()
         out[name] = {
             "fwd_ms": t_f, "bwd_ms": t_b, "step_gpix_s": px / ((t_f + t_b) * 1e-3) / 1e9,
             "fwd_frac_of_measured_hbm": 8 * px / (t_f * 1e-3) / 1e9 / _peaks()[0],
             "bwd_frac_of_measured_hbm": 14 * px / (t_b * 1e-3) / 1e9 / _peaks()[0],
+            "fwd_frac_of_fma_pipe": FMA_LANE_CYCLES_PER_PX["fwd"] * px / (t_f * 1e-3) / fma_peak,
+            "bwd_frac_of_fma_pipe": FMA_LANE_CYCLES_PER_PX["bwd"] * px / (t_b * 1e-3) / fma_peak,
             "errors": "tests/test_gpu_precision.py (sampled outputs against the FP64 oracle)"}
         del img, g, o, gi, ws
     return out
