@@ -144,22 +144,45 @@ struct WSlot {
     static constexpr uint32_t kLaneImg = kWCols * 3 * sizeof(TI);  // 48 or 96
     static constexpr uint32_t kLaneCot = kWCols * sizeof(TG);      // 16 or 32
 
-    // The lane's pieces of a slot (shared address of the slot's start).
+    // The lane's pieces of a slot (shared address of the slot's start). Pieces of 32 or 96 bytes
+    // (float32) put the 8 lanes of a quarter warp on only 4 of the 8 16-byte bank groups; lanes
+    // 4..7 of each quarter therefore read the 16-byte chunks of each pair in swapped order (which
+    // lands them on the other 4 groups) and swap the pair back in registers.
+    __device__ __forceinline__ static uint4 pick(bool swap, const uint4& a, const uint4& b) {
+        return make_uint4(swap ? b.x : a.x, swap ? b.y : a.y, swap ? b.z : a.z, swap ? b.w : a.w);
+    }
     __device__ __forceinline__ static void read(uint32_t slot, int lane, bool g_in, WideRaw<TI>& r, float gv[8]) {
         constexpr int NQ = kLaneImg / 16;
+        constexpr bool kSwizzle = SHINE_WIDE_BWD_SWAP_PAIRS && sizeof(TI) == 4;
         const uint32_t im = slot + lane * kLaneImg;
+        const uint32_t flip = kSwizzle ? (uint32_t)(lane >> 2) & 1u : 0u;
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
-            const float4 t = lds128(im + 16 * i);
+            const float4 t = lds128(im + 16 * ((uint32_t)i ^ flip));
             r.q[i] = make_uint4(__float_as_uint(t.x), __float_as_uint(t.y), __float_as_uint(t.z), __float_as_uint(t.w));
+        }
+        if constexpr (kSwizzle) {
+#pragma unroll
+            for (int i = 0; i < NQ; i += 2) {
+                const uint4 a = r.q[i], b = r.q[i + 1];
+                r.q[i] = pick(flip, a, b);
+                r.q[i + 1] = pick(flip, b, a);
+            }
         }
         if (g_in) {
             WideCot<TG> c;
             const uint32_t co = slot + kImg + lane * kLaneCot;
+            constexpr bool kSwizzleG = SHINE_WIDE_BWD_SWAP_PAIRS && sizeof(TG) == 4;
+            const uint32_t gflip = kSwizzleG ? (uint32_t)(lane >> 2) & 1u : 0u;
 #pragma unroll
             for (int i = 0; i < (int)(kLaneCot / 16); ++i) {
-                const float4 t = lds128(co + 16 * i);
+                const float4 t = lds128(co + 16 * ((uint32_t)i ^ gflip));
                 c.q[i] = make_uint4(__float_as_uint(t.x), __float_as_uint(t.y), __float_as_uint(t.z), __float_as_uint(t.w));
+            }
+            if constexpr (kSwizzleG) {
+                const uint4 a = c.q[0], b = c.q[1];
+                c.q[0] = pick(gflip, a, b);
+                c.q[1] = pick(gflip, b, a);
             }
             cot8<TG>(c, gv);
         } else {

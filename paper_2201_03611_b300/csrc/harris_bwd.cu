@@ -170,7 +170,7 @@ int resident_warps(K kernel, int threads, size_t smem) {
 
 template <typename TI, typename TG>
 cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
-    constexpr int NS = SHINE_WIDE_BWD_STAGES;
+    constexpr int NS = sizeof(TI) == 4 ? SHINE_WIDE_BWD_STAGES_F32 : SHINE_WIDE_BWD_STAGES;
     const size_t smem = wide_adj_smem<TI, TG>(NS);
     auto kern = harris_bwd_wide_kernel<TI, TG, NS>;
     a.x0 = SHINE_WIDE_BWD_ORIGIN;
@@ -194,7 +194,7 @@ cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
     // wide kernel (measured on 8192^2: bf16 0.409 -> 0.388 ms, fp16 0.440 -> 0.410 ms; float32
     // 0.413 -> 0.478 ms, where its 96-byte lane pieces meet 2-way bank conflicts, so float32
     // images stay on the four-column kernel)
-    if constexpr (SHINE_WIDE_BWD && sizeof(TI) == 2) {
+    if constexpr (SHINE_WIDE_BWD && (sizeof(TI) == 2 || SHINE_WIDE_BWD_F32)) {
         if (a.tma && !a.valid && a.rout == nullptr) return launch_bwd_wide_t<TI, TG>(a, max_warps, s, used);
     }
     // ring depth: the adjoint alone takes bwd_stages<TI>(), the fused forward+adjoint (which also

@@ -38,6 +38,15 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_WIDE_BWD_STAGES
 #define SHINE_WIDE_BWD_STAGES 4   // its staging ring (rows)
 #endif
+#ifndef SHINE_WIDE_BWD_F32
+#define SHINE_WIDE_BWD_F32 0      // float32 images take it too
+#endif
+#ifndef SHINE_WIDE_BWD_STAGES_F32
+#define SHINE_WIDE_BWD_STAGES_F32 3  // its staging ring for float32 images (8 warps x 28 KB)
+#endif
+#ifndef SHINE_WIDE_BWD_SWAP_PAIRS
+#define SHINE_WIDE_BWD_SWAP_PAIRS 1  // conflict-free float32 reads of the staged pieces
+#endif
 #ifndef SHINE_WIDE_BWD_ORIGIN
 #define SHINE_WIDE_BWD_ORIGIN 0   // first output column of its segment 0 (a multiple of 8)
 #endif
