@@ -246,3 +246,34 @@ def test_bwd_16bit_wide_path(shine, dtype, shape):
     ref = cref.backward(img.cpu(), g.cpu(), 0.05, wx, wy, "clamp", with_abs=True)
     assert U.rel(U.host(wide[0]), ref[0]) <= U.TOL_16
     U.assert_params(wide[1:], ref[1:])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("shape", [(3, 70000), (70001, 8), (2, 65536), (5, 1), (1, 131072)])
+def test_extreme_aspect_ratios(shine, dtype, shape):
+    """Very wide and very tall images (hundreds of column segments of a few rows each, or one
+    segment of tens of thousands of rows): forward and adjoint against the oracle."""
+    h, w = shape
+    img = wl.random_image(h, w, seed=h + 7 * w).to(dtype)
+    g = wl.random_cotangent(h, w, seed=h + 3 * w).to(dtype)
+    wx, wy = wl.random_weights(w % 97)
+    k, dwx, dwy = U.dev_params(0.04, wx, wy)
+    tol = U.TOL_F32 if dtype == torch.float32 else U.TOL_16
+    r = shine.pipeline_fwd(img.cuda(), k, dwx, dwy, "clamp")
+    gi, gk, gwx, gwy = shine.pipeline_bwd(img.cuda(), g.cuda(), k, dwx, dwy, "clamp")
+    torch.cuda.synchronize()
+    assert U.rel(U.host(r), cref.forward(img, 0.04, wx, wy, "clamp")) <= tol
+    ref = cref.backward(img, g, 0.04, wx, wy, "clamp", with_abs=True)
+    assert U.rel(U.host(gi), ref[0]) <= (U.TOL_GIMG if dtype == torch.float32 else U.TOL_16)
+    U.assert_params((gk, gwx, gwy), ref[1:])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_zero_cotangent_gives_exact_zeros(shine, dtype):
+    """A zero cotangent: every cotangent output is exactly zero (both adjoint kernels)."""
+    for w in (256, 250):  # aligned 16-bit rows (eight-column kernel) and not
+        img = wl.random_image(97, w, seed=w).to(dtype).cuda()
+        g = torch.zeros(97, w, dtype=dtype, device="cuda")
+        k, dwx, dwy = U.dev_params(0.04, *wl.random_weights(3))
+        for t in shine.pipeline_bwd(img, g, k, dwx, dwy, "clamp"):
+            assert torch.count_nonzero(t) == 0
