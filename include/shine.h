@@ -384,6 +384,17 @@ SHINE_API shine_status shine_mv(const void* A, int64_t M, int64_t N, int64_t lda
 SHINE_API shine_status shine_wait_status(int* failed, int clear);
 
 /*
+ * Index checks of debug builds (no counterpart in the paper; a stand-in for a memory checker).
+ * The library built with SHINE_DEBUG_BOUNDS=1 (libshine_debug.so) checks the row and column
+ * ranges of the Harris kernels' global loads, stores and copies and of their shared-memory
+ * staging, and on a violation sets a bit of one word per GPU (bit 0 forward loads, 1 forward
+ * stores, 2 forward copies, 3 adjoint copies, 4 adjoint stores, 5 shared memory) without
+ * trapping. *instrumented is 1 in such a build, 0 otherwise (then *bits is always 0); *bits is
+ * the word, cleared when clear != 0. Synchronises with the device in a debug build.
+ */
+SHINE_API shine_status shine_debug_bounds_status(int* instrumented, unsigned int* bits, int clear);
+
+/*
  * Host-side view of the work partition the kernels use (no counterpart in the paper; for tests
  * and tuning): the (segment, row) units [*lo, *hi), in segment-major order, that warp w of t
  * takes over nseg column segments of rows rows; band_major != 0 selects the band-major layout

@@ -9,7 +9,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libshine.so")
+# SHINE_LIBRARY selects another build of the library (the index-checking libshine_debug.so).
+LIB_PATH = os.environ.get("SHINE_LIBRARY") or os.path.join(_HERE, "libshine.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "libshine_debug.so")
 
 SHINE_OK, SHINE_ERR_INVALID_ARG, SHINE_ERR_ALIGNMENT, SHINE_ERR_WORKSPACE, SHINE_ERR_UNSUPPORTED, \
     SHINE_ERR_CUDA = range(6)
@@ -61,6 +63,7 @@ def lib() -> ctypes.CDLL:
         "shine_pipeline_host": (st, [p, p, p, p, i64, i64, f, f, p, p, p, p, p, p, p, p, p, sz, i32, p]),
         "shine_mv": (st, [p, i64, i64, i64, f, p, p, p]),
         "shine_wait_status": (st, [ctypes.POINTER(f), f]),
+        "shine_debug_bounds_status": (st, [ctypes.POINTER(f), ctypes.POINTER(ctypes.c_uint), f]),
         "shine_partition": (st, [i64, i64, i64, i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "shine_selftest_bounded_wait": (st, [i32, p, p]),
         "shine_iterate_sum": (st, [p, i64, i32, i32, p, p]),

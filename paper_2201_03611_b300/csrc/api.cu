@@ -27,6 +27,10 @@ __device__ unsigned int g_wait_flag;
 std::mutex g_wait_mutex;
 unsigned int* g_wait_ptr[64] = {};
 
+// Debug builds: the index-check violation word, one per GPU (see SHINE_CHECK).
+__device__ unsigned int g_bounds_flag;
+unsigned int* g_bounds_ptr[64] = {};
+
 shine_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SHINE_OK;
     g_last_cuda_error = (int)e;
@@ -47,6 +51,19 @@ unsigned int* wait_flag() {
         g_wait_ptr[dev] = static_cast<unsigned int*>(p);
     }
     return g_wait_ptr[dev];
+}
+
+unsigned int* bounds_flag() {
+    if constexpr (!SHINE_DEBUG_BOUNDS) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_wait_mutex);
+    if (g_bounds_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bounds_flag) != cudaSuccess) return nullptr;
+        g_bounds_ptr[dev] = static_cast<unsigned int*>(p);
+    }
+    return g_bounds_ptr[dev];
 }
 
 int sm_count() {
@@ -79,6 +96,7 @@ void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_imag
     g.band_rows = band_rows;
     g.nband = (g.yhi - g.ylo + band_rows - 1) / band_rows;
     g.nwarps = 0;
+    g.dbg = bounds_flag();
 }
 
 Geometry fwd_geometry(int64_t H, int64_t W, int border) {
@@ -162,6 +180,24 @@ shine_status shine_wait_status(int* failed, int clear) {
         const unsigned int zero = 0;
         e = cudaMemcpyToSymbol(g_wait_flag, &zero, sizeof zero);
         if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SHINE_OK;
+}
+
+shine_status shine_debug_bounds_status(int* instrumented, unsigned int* bits, int clear) {
+    if (!instrumented || !bits) return SHINE_ERR_INVALID_ARG;
+    *instrumented = SHINE_DEBUG_BOUNDS;
+    *bits = 0;
+    if constexpr (SHINE_DEBUG_BOUNDS) {
+        unsigned int v = 0;
+        cudaError_t e = cudaMemcpyFromSymbol(&v, g_bounds_flag, sizeof v);
+        if (e != cudaSuccess) return cuda_status(e);
+        *bits = v;
+        if (clear) {
+            const unsigned int zero = 0;
+            e = cudaMemcpyToSymbol(g_bounds_flag, &zero, sizeof zero);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
     }
     return SHINE_OK;
 }

@@ -61,6 +61,7 @@ struct BatchArgs {
     int valid;
     int origin;              // first output column of segment 0
     unsigned int* err;       // set when a bounded wait gave up (bulk staging)
+    unsigned int* dbg;       // debug builds: index-check violation word
     unsigned int* counter;
     double* partials;        // [kParamSlots][ntiles]
     const float* kappa;      // [n]
@@ -69,8 +70,9 @@ struct BatchArgs {
 };
 
 __device__ __forceinline__ void dev_geometry(Geometry& g, int H, int W, int valid, bool full_image, int br,
-                                             int x0) {
+                                             int x0, unsigned int* dbg) {
     g.H = H; g.W = W; g.valid = valid;
+    g.dbg = dbg;
     if (valid && !full_image) {
         g.xlo = 2; g.xhi = W - 2; g.ylo = 2; g.yhi = H - 2; g.ox = 2; g.oy = 2;
     } else {
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
         const int H = (int)d.H, W = (int)d.W;
         if constexpr (!FWD_BWD) {
             FwdArgs a;
-            dev_geometry(a, H, W, b.valid, false, b.band_rows[img], b.origin);
+            dev_geometry(a, H, W, b.valid, false, b.band_rows[img], b.origin, b.dbg);
             a.img = d.img; a.img_pitch = d.img_pitch; a.out = d.out; a.out_pitch = d.out_pitch;
             a.kappa = b.kappa + img; a.wx = b.wx; a.wy = b.wy;
             a.aligned = dev_aligned(d.img, d.img_pitch, sizeof(T), chunk);
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kBatchThreads) harris_batched_kernel(BatchArgs
             }
         } else {
             BwdArgs a;
-            dev_geometry(a, H, W, b.valid, true, b.band_rows[img], b.origin);
+            dev_geometry(a, H, W, b.valid, true, b.band_rows[img], b.origin, b.dbg);
             a.img = d.img; a.img_pitch = d.img_pitch;
             a.gout = d.grad_out; a.gout_pitch = d.gout_pitch;
             a.gho = b.valid ? H - 4 : H; a.gwo = b.valid ? W - 4 : W;
@@ -487,6 +489,7 @@ shine_status shine_pipeline_batched(const shine_plan* plan, const shine_image_de
     b.n = plan->n;
     b.valid = plan->border == SHINE_VALID;
     b.origin = plan->origin;
+    b.dbg = bounds_flag();
     // workspace header: the bounded-wait failure word (read by shine_workspace_status), then the
     // tile counter
     b.err = static_cast<unsigned int*>(workspace);

@@ -547,6 +547,7 @@ __device__ __forceinline__ void wide_adj_strip(const BwdArgs& a, const Params& P
                 }
             }
             if (producer) {
+                SHINE_CHECK(a.dbg, u >= 0 && u < H && (!full || !a.gimg_vec || (x >= 0 && x + kWCols <= W)), kDbgBwdStore);
                 TI* orow = gimg + (int64_t)u * a.gimg_pitch + (int64_t)x * 3;
                 float o[24];
 #pragma unroll

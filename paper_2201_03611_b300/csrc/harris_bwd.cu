@@ -112,6 +112,10 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_wide_kernel(BwdArgs a)
     const uint32_t ring0 = base + (uint32_t)warp * NS * WSlot<TI, TG>::kBytes;
     WRings rg;
     rg.init(base + kWarps * NS * (WSlot<TI, TG>::kBytes + 8) + (uint32_t)warp * kWRingBytes, lane);
+    SHINE_CHECK(a.dbg, smem_in(ring0, NS * WSlot<TI, TG>::kBytes) &&
+                           smem_in(base + kWarps * NS * (WSlot<TI, TG>::kBytes + 8) + (uint32_t)warp * kWRingBytes,
+                                   kWRingBytes),
+                kDbgSmem);
     rg.acc_zero();
     BulkState bulk;
     bulk.seq = 0;
@@ -137,8 +141,15 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_wide_kernel(BwdArgs a)
         const bool edge = (xb - kWCols < 0) || (xb + kWSegOut + kWCols > a.W);
         if (edge) {
             WAdjLanes<TI, TG, NS> src(a, ring0, lane, x, y0 - 4, n);
+            // a lane whose columns all lie outside the row copies nothing (zero-fill only)
+            SHINE_CHECK(a.dbg, src.vbytes_img == 0 ||
+                                   (x >= 0 && x * 3 * (int)sizeof(TI) + src.vbytes_img <= 3 * a.W * (int)sizeof(TI) &&
+                                    x * (int)sizeof(TG) + src.vbytes_cot <= a.gwo * (int)sizeof(TG)),
+                        kDbgBwdStage);
             wide_adj_strip<TI, true, false>(a, P, lane, x, y0, y1, src, rg, nullptr);
         } else {
+            SHINE_CHECK(a.dbg, xb - kWCols >= 0 && xb - kWCols + kWSegLoad <= a.W && xb - kWCols + kWSegLoad <= a.gwo,
+                        kDbgBwdStage);
             WAdjBulk<TI, TG, NS> src(bulk, a, ring0, lane, xb - kWCols, y0 - 4, n);
             wide_adj_strip<TI, false, true>(a, P, lane, x, y0, y1, src, rg, &bulk.failed);
         }

@@ -106,6 +106,16 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
 
     // Bulk staging: the warp's segment starts 4 columns left of the lane-1 column.
     const int xs = x - 4 * lane;
+    if constexpr (TMA) {
+        SHINE_CHECK(a.dbg, xs >= 0 && xs + kSegLoad <= W, kDbgBwdStage);
+        SHINE_CHECK(a.dbg, xs - a.ox >= 0 && xs - a.ox + kSegLoad <= a.gwo, kDbgBwdStage);
+    } else if constexpr (ALIGNED && !EDGE) {
+        SHINE_CHECK(a.dbg, x >= 0 && x + kCols <= W, kDbgBwdStage);
+    }
+    if constexpr (ALIGNED) {
+        SHINE_CHECK(a.dbg, smem_in(smem_u32(ring), (uint32_t)((NS - 1) * PixelRows<TI, NS, EDGE, ALIGNED>::kSlot + 12) *
+                                                       (uint32_t)sizeof(TI)), kDbgSmem);
+    }
     constexpr uint32_t kImgBytes = kSegLoad * 3 * sizeof(TI), kCotBytes = kSegLoad * sizeof(TG);
     int last_issued = -1, last_done = -1;  // bulk staging: rows issued / waited for successfully
     // ring position of the next row to stage, advanced one slot per step (no division per step)
@@ -260,6 +270,8 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 float R[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) R[j] = response(S2[j].x, Sxy[j], S2[j].y, P.kappa);
+                SHINE_CHECK(a.dbg, sr >= rlo && sr < rhi && (EDGE || !rvec || a.valid || (x >= 0 && x + kCols <= W)),
+                            kDbgBwdStore);
                 TI* orow = rout + (int64_t)(sr - rlo) * rpitch;
                 if (!EDGE && rvec && !a.valid) {
                     if constexpr (sizeof(TI) == 4) {
@@ -395,6 +407,7 @@ __device__ __forceinline__ void bwd_strip(const BwdArgs& a, const Params& P, int
                 }
             }
             if (producer) {
+                SHINE_CHECK(a.dbg, u >= 0 && u < H && (EDGE || !a.gimg_vec || (x >= 0 && x + kCols <= W)), kDbgBwdStore);
                 TI* orow = gimg + (int64_t)u * a.gimg_pitch + (int64_t)x * 3;
                 float o[12];
 #pragma unroll

@@ -151,6 +151,15 @@ __device__ __forceinline__ uint2 lds64(uint32_t addr) {
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(addr) : "memory");
     return v;
 }
+// Debug builds: whether [addr, addr + bytes) lies inside the CTA's dynamic shared memory.
+__device__ __forceinline__ bool smem_in(uint32_t addr, uint32_t bytes) {
+    extern __shared__ unsigned char shine_dyn_smem[];
+    uint32_t size;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(shine_dyn_smem));
+    return addr >= base && addr + bytes <= base + size;
+}
+
 // Generic-proxy accesses to shared memory before async-proxy (bulk copy) writes to it.
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

@@ -57,7 +57,10 @@ __device__ __forceinline__ void wide_strip_elem(const FwdArgs& a, const Params& 
         widen10<EDGE>(c, g10, x, W);
     };
     auto store = [&](int y, const float R[8]) {
-        if (producer) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+        if (producer) {
+            SHINE_CHECK(a.dbg, y >= a.ylo && y < a.yhi, kDbgFwdStore);
+            store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+        }
     };
     wide_strip_core<EDGE>(P, x, W, H, y0, y1, take, store, [] { return true; });
 }
@@ -79,6 +82,8 @@ __device__ __forceinline__ void wide_strip_pf(const FwdArgs& a, const Params& P,
     const uint32_t pbytes = (uint32_t)((phi - plo) * 3 * (int)sizeof(TI)) & ~15u;
     const char* prow = reinterpret_cast<const char*>(img + (int64_t)plo * 3);
     const int64_t pitch_b = a.img_pitch * (int64_t)sizeof(TI);
+    SHINE_CHECK(a.dbg, pbytes <= (uint32_t)((phi - plo) * 3 * (int)sizeof(TI)), kDbgFwdStage);
+    if constexpr (!EDGE) SHINE_CHECK(a.dbg, x >= 0 && x + kWCols <= W, kDbgFwdLoad);
     int pr = y0 - 2;  // next row to prefetch (unclamped)
     const uint32_t lead = lane == 0 && pbytes != 0;
     auto prefetch_next = [&]() {
@@ -100,6 +105,8 @@ __device__ __forceinline__ void wide_strip_pf(const FwdArgs& a, const Params& P,
     };
     auto store = [&](int y, const float R[8]) {
         if (producer) {
+            SHINE_CHECK(a.dbg, y >= a.ylo && y < a.yhi, kDbgFwdStore);
+            if constexpr (!EDGE) SHINE_CHECK(a.dbg, x >= a.xlo && x + kWCols <= a.xhi && a.ox == 0 && a.oy == 0, kDbgFwdStore);
             if constexpr (EDGE) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
             else store_row_interior(a, out + (int64_t)y * a.out_pitch + x, R);
         }
@@ -115,7 +122,12 @@ __device__ __forceinline__ void wide_strip_edge(const FwdArgs& a, const Params& 
     TO* out = static_cast<TO*>(a.out);
     const bool producer = lane >= 1 && lane <= 30;
     const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    SHINE_CHECK(a.dbg, smem_in(ring0, NS * WideLaneStage<TI, NS>::kSlotBytes), kDbgSmem);
     WideLaneStage<TI, NS> src(static_cast<const TI*>(a.img), a.img_pitch, x, W, H, ring0, lane, y0 - 2, n);
+    // a lane whose columns all lie outside the row copies nothing (zero-fill only)
+    SHINE_CHECK(a.dbg, src.valid_bytes == 0 || (x >= 0 && (x + kWCols <= W ? kWCols : W - x) * 3 * (int)sizeof(TI) ==
+                                                              src.valid_bytes),
+                kDbgFwdStage);
     auto take = [&](float g10[10]) {
         WideRaw<TI> r;
         src.take_raw(r);
@@ -124,7 +136,10 @@ __device__ __forceinline__ void wide_strip_edge(const FwdArgs& a, const Params& 
         widen10<true>(c, g10, x, W);
     };
     auto store = [&](int y, const float R[8]) {
-        if (producer) store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+        if (producer) {
+            SHINE_CHECK(a.dbg, y >= a.ylo && y < a.yhi, kDbgFwdStore);
+            store_row(a, out + (int64_t)(y - a.oy) * a.out_pitch, x, a.out_vec, R);
+        }
     };
     wide_strip_core<true>(P, x, W, H, y0, y1, take, store, [] { return true; });
     src.finish();
@@ -136,6 +151,9 @@ __device__ __forceinline__ void wide_strip_bulk(const FwdArgs& a, const Params& 
                                                 uint32_t ring0, WideBulkState& bs) {
     const int H = a.H;
     const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    SHINE_CHECK(a.dbg, x - kWCols * lane >= 0 && x - kWCols * lane + kWSegLoad <= a.W, kDbgFwdStage);
+    SHINE_CHECK(a.dbg, smem_in(ring0, NS * WideBulk<TI, NS>::kBytes), kDbgSmem);
+    SHINE_CHECK(a.dbg, y0 >= a.ylo && y1 <= a.yhi && x >= a.xlo && x + kWCols <= a.xhi, kDbgFwdStore);
     WideBulk<TI, NS> src(bs, static_cast<const TI*>(a.img), a.img_pitch, x - kWCols * lane, ring0, lane, y0 - 2, n, H);
     TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
     const int64_t opitch = a.out_pitch;

@@ -50,6 +50,8 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_WIDE_BWD_ORIGIN
 #define SHINE_WIDE_BWD_ORIGIN 0   // first output column of its segment 0 (a multiple of 8)
 #endif
+static_assert(SHINE_WIDE_BWD_ORIGIN % 8 == 0 && SHINE_WIDE_BWD_ORIGIN > -240 && SHINE_WIDE_BWD_ORIGIN <= 0,
+              "the eight-column adjoint needs whole lanes inside or outside the image");
 #ifndef SHINE_WIDE_BWD_EDGE_WEIGHT4
 #define SHINE_WIDE_BWD_EDGE_WEIGHT4 8  // an edge-segment row weighs this / 4 interior rows (measured:
 #endif                              // 8 best of 6, 8, 10 on 8192^2 bf16)
@@ -90,7 +92,31 @@ struct Geometry {
     int nseg;          // column segments of kSegOut output columns
     int nband, band_rows;  // row bands (tile lists of the batched path)
     int nwarps;        // single-image kernels: warps sharing the nseg x rows work units
+    unsigned int* dbg; // debug builds: the index-check violation word (null otherwise)
 };
+
+// Debug builds (compiled with SHINE_DEBUG_BOUNDS=1, the library libshine_debug.so) check the index
+// ranges of the Harris kernels' global loads, stores and copies and of their shared-memory
+// staging against the image, output and ring extents, and on a violation set bit `bit` of the
+// violation word (no trap; the access still happens as it would in a release build, so a debug
+// run gives the release results). Release builds compile the checks away.
+#ifndef SHINE_DEBUG_BOUNDS
+#define SHINE_DEBUG_BOUNDS 0
+#endif
+enum : int {
+    kDbgFwdLoad = 0,     // forward: image row or column range of a vector load
+    kDbgFwdStore = 1,    // forward: output row or column range of a store
+    kDbgFwdStage = 2,    // forward: bulk copy or per-lane copy source range
+    kDbgBwdStage = 3,    // adjoint: image or cotangent copy source range
+    kDbgBwdStore = 4,    // adjoint: d img or R store range
+    kDbgSmem = 5,        // a staging access outside the CTA's dynamic shared memory
+};
+#define SHINE_CHECK(dbgp, cond, bit)                                           \
+    do {                                                                       \
+        if constexpr (SHINE_DEBUG_BOUNDS) {                                    \
+            if (!(cond) && (dbgp) != nullptr) atomicOr((dbgp), 1u << (bit));   \
+        }                                                                      \
+    } while (0)
 
 // Balanced split of n work units over t workers: worker w gets [lo, hi), sizes differ by <= 1.
 __host__ __device__ inline void balanced_slice(int64_t n, int64_t t, int64_t w, int64_t& lo, int64_t& hi) {

@@ -18,6 +18,9 @@ bool border_ok(int b);
 int sm_count();
 // Device address of the library's bounded-wait failure flag on the current device (or null).
 unsigned int* wait_flag();
+// Debug builds: device address of the index-check violation word on the current device; null in
+// release builds.
+unsigned int* bounds_flag();
 shine_status check_shape(int64_t H, int64_t W, int border);
 bool aligned_to(const void* p, size_t a);
 void fill_geometry(Geometry& g, int64_t H, int64_t W, int border, bool full_image, int band_rows);

@@ -33,12 +33,15 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, name), name
 
 
-def test_only_the_abi_is_exported():
+def _exported(path):
     import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    return {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+
+
+def test_only_the_abi_is_exported():
     from paper_2201_03611_b300._lib import LIB_PATH
-    out = subprocess.run(["nm", "-D", "--defined-only", LIB_PATH], capture_output=True, text=True).stdout
-    text = [ln.split()[-1] for ln in out.splitlines() if " T " in ln]
-    assert set(text) == set(_declared())
+    assert _exported(LIB_PATH) == set(_declared())
 
 
 def test_status_strings(L):
@@ -119,3 +122,12 @@ def test_package_import_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(ImportError):
         _lib.lib()
     importlib.reload(_lib)
+
+
+def test_debug_build_exports_the_same_symbols():
+    """libshine_debug.so (index checks compiled in) offers exactly the release library's ABI."""
+    import os
+    from paper_2201_03611_b300 import _lib
+    if not os.path.exists(_lib.DEBUG_LIB_PATH):
+        pytest.skip("libshine_debug.so not built")
+    assert _exported(_lib.DEBUG_LIB_PATH) == _exported(_lib.LIB_PATH)
