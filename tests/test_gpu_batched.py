@@ -28,7 +28,7 @@ def _batch(n, dtype, seed, lo=5, hi=300, border="clamp", pad16=True):
     return b, imgs, ws
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("border", ["clamp", "valid"])
 @pytest.mark.parametrize("pad16", [True, False])
 def test_batched_equals_per_image(shine, dtype, border, pad16):
