@@ -271,13 +271,13 @@ shine_status shine_corners(const void* img, int64_t H, int64_t W, int64_t img_pi
     a.kappa = kappa; a.wx = wx; a.wy = wy;
     const size_t chunk = si == 4 ? 16 : 8;
     a.aligned = aligned_to(img, chunk) && ((size_t)img_pitch * si) % chunk == 0;
-    a.out_vec = out && border == SHINE_CLAMP && aligned_to(out, 4 * so) && ((size_t)out_pitch * so) % (4 * so) == 0;
+    a.out_vec = out && border == SHINE_CLAMP && aligned_to(out, 16) && ((size_t)out_pitch * so) % 16 == 0;
     a.tma = SHINE_FWD_TMA && aligned_to(img, 16) && ((size_t)img_pitch * si) % 16 == 0;
     a.err = wait_flag();
     c.mask = mask;
     c.mask_pitch = mask_pitch;
     c.threshold = threshold;
-    c.mask_vec = border == SHINE_CLAMP && aligned_to(mask, 4) && mask_pitch % 4 == 0;
+    c.mask_vec = border == SHINE_CLAMP && aligned_to(mask, 8) && mask_pitch % 8 == 0;
     return cuda_status(launch_harris_corners(c, dt, out ? out_dt : dt, static_cast<cudaStream_t>(stream)));
 }
 

@@ -3,43 +3,56 @@
 // pipeline, one more map over slide2D(3,1) windows fused after A5 (map fusion, Sec. 4.2). R
 // only reaches global memory when the caller asks for it; the mask is one byte per output pixel.
 //
-// A warp streams its strip exactly as the forward does, over one extra R row above and below
-// the rows it owns (clipped to the output region). Each R row is widened to 6 columns (its 4
-// and one from each neighbouring lane: lanes 0 and 31 hold valid R at the columns next to the
-// segment) and reduced to horizontal 3-maxima; running maxima of the last rows then decide row
-// y-1 when row y arrives.
+// A warp streams its strip exactly as the forward does (eight columns per lane, the row sources
+// of harris_fwd_wide.cuh), over one extra R row above and below the rows it owns (clipped to the
+// output region). Each R row is widened to 10 columns (its 8 and one from each neighbouring
+// lane: lanes 0 and 31 hold valid R at the columns next to the segment) and reduced to
+// horizontal 3-maxima; a row is decided once the row below it has arrived.
 #include <algorithm>
 #include <type_traits>
 
-#include "harris_fwd_strip.cuh"
+#include "harris_fwd_wide.cuh"
 #include "shine_host.h"
 
 namespace shine {
 
 namespace {
 
-// float32 register cap: the bulk-staged variant fits 128 registers (16 warps per SM) without
-// spilling; the others keep 168 (12 warps), where they do not spill either.
-template <typename TI, typename TO, int D, bool ALIGNED, bool TMA>
-__global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? (TMA ? 4 : 3) : SHINE_FWD_MIN_BLOCKS)
-    harris_corners_kernel(CornerArgs c) {
+// Maximum that returns NaN when either operand is NaN (max.NaN): a NaN in a window makes its
+// maximum NaN, and no value compares >= NaN, so a pixel with a NaN neighbour is no corner, as
+// the definition (R >= each neighbour) has it.
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float max3_nan(float a, float b, float c) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// out_vec: R rows allow 16-byte stores; mask_vec: mask rows allow 8-byte stores.
+template <typename TI, typename TO, bool SMEM>
+__global__ void __launch_bounds__(kFwdThreads, SHINE_WIDE_CORNERS_MIN_BLOCKS) harris_corners_kernel(CornerArgs c) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const FwdArgs& a = c.f;
-    constexpr int NS = kFwdBulkStages;
+    constexpr int NS = SHINE_WIDE_BULK_STAGES;
+    constexpr uint32_t kSlotBytes = kWSegLoad * 3 * sizeof(TI);
+    constexpr bool kBulk = sizeof(TI) == 4 ? SHINE_WIDE_BULK_F32 : SHINE_WIDE_BULK_16;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (kFwdThreads / 32) + warp;
     if (gw >= a.nwarps) return;  // whole warp
-    FwdBulk bulk;
-    bulk.seq = 0;
-    bulk.failed = false;
-    TI* ring = nullptr;
-    if constexpr (TMA) {
-        ring = reinterpret_cast<TI*>(smem_raw) + warp * NS * kLanes * 12 + lane * 12;
-        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kFwdThreads * NS * 12 * sizeof(TI)) + warp * NS;
-        bulk.bars = smem_u32(bars);
+    WideBulkState bs;
+    bs.seq = 0;
+    bs.failed = false;
+    uint32_t ring0 = 0;
+    if constexpr (SMEM && kBulk) {
+        ring0 = smem_u32(smem_raw) + (uint32_t)warp * NS * kSlotBytes;
+        bs.bars = smem_u32(smem_raw) + (uint32_t)(kFwdThreads / 32) * NS * kSlotBytes + (uint32_t)warp * NS * 8;
         if (lane == 0)
-            for (int i = 0; i < NS; ++i) mbar_init(bulk.bars + 8 * i, 1);
+            for (int i = 0; i < NS; ++i) mbar_init(bs.bars + 8 * i, 1);
         mbar_init_fence();
         __syncwarp();
     }
@@ -47,116 +60,121 @@ __global__ void __launch_bounds__(kFwdThreads, sizeof(TI) == 4 ? (TMA ? 4 : 3) :
     load_params(P, a.wx, a.wy, a.kappa);
     const bool producer = lane >= 1 && lane <= 30;
     const float kNegInf = __int_as_float(0xff800000);
+    TO* out = static_cast<TO*>(a.out);
     const int64_t rows = a.yhi - a.ylo;
     int64_t lo, hi;
     warp_work(SHINE_FWD_BAND_MAJOR, a.nseg, rows, a.nwarps, gw, lo, hi, SHINE_FWD_EDGE_WEIGHT4);
-    while (lo < hi && !bulk.failed) {
+    while (lo < hi && !bs.failed) {
         const int seg = (int)(lo / rows);
         const int r0 = (int)(lo % rows);
         const int r1 = (int)(rows < r0 + (hi - lo) ? rows : r0 + (hi - lo));
-        const int xb = a.x0 + seg * kSegOut;
-        const int x = xb - 4 + 4 * lane;
-        const bool edge = (xb - 4 < 0) || (xb + kSegOut + 4 > a.W) || a.valid;
-        const int y0 = a.ylo + r0, y1 = a.ylo + r1;                      // rows this warp decides
-        const int ys = y0 - 1 > a.ylo ? y0 - 1 : a.ylo;                  // R rows it computes
+        const int xb = a.x0 + seg * kWSegOut;
+        const int x = xb - kWCols + kWCols * lane;
+        const bool edge = (xb - kWCols < 0) || (xb + kWSegOut + kWCols > a.W) || a.valid;
+        const int y0 = a.ylo + r0, y1 = a.ylo + r1;      // rows this warp decides
+        const int ys = y0 - 1 > a.ylo ? y0 - 1 : a.ylo;  // R rows it computes
         const int ye = y1 + 1 < a.yhi ? y1 + 1 : a.yhi;
-        // Columns of the lane inside the output region (others read as -inf: no neighbour).
-        bool cin[4];
+        // Row y-1 is a corner where R(y-1) exceeds the threshold and is >= every value of its 3x3
+        // window, i.e. >= max(hm(y-2), hm(y-1)) (tested when row y-1 arrives, one bit per column
+        // in cand) and >= hm(y) (tested when row y arrives); hm are horizontal 3-maxima that
+        // propagate NaN. State: cand, hb = hm(y-1), cen = R(y-1).
+        uint32_t cand = 0;
+        float hb[8], cen[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cin[j] = x + j >= a.xlo && x + j < a.xhi;
-        // Push form of the 3x3 maximum (max is exact, so any grouping gives the same value):
-        // each R row arrives as its horizontal 3-maxima hm; the decision of row y-1 needs
-        // max(hm(y-2), hm(y-1), hm(y)) and R(y-1) itself.
-        float ha[4], hb[4], cen[4];  // max(hm(y-2), hm(y-1)); hm(y-1); R(y-1)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ha[j] = hb[j] = cen[j] = kNegInf;
-
-        // Decide row y: corner where the centre exceeds the threshold and equals the maximum of
-        // its 3x3 window (that is, is >= each of its 8 neighbours). E: an edge segment (or the
-        // VALID region), where some of the lane's columns may lie outside the output region;
-        // interior segments know at compile time that all four are inside.
-        auto emit = [&](auto edge_tag, int y, const float nb[4]) {
+        for (int j = 0; j < 8; ++j) hb[j] = cen[j] = kNegInf;
+        // a lane column inside the output region (others read as -inf: no neighbour)
+        auto col_in = [&](int j) { return x + j >= a.xlo && x + j < a.xhi; };
+        // decide row y (cand and cen describe it) against the horizontal maxima of the row below
+        // (-inf at the region's last row)
+        auto emit = [&](auto edge_tag, int y, const float* below) {
             constexpr bool E = decltype(edge_tag)::value;
-            uint32_t bits = 0;
+            uint32_t b0 = 0, b1 = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const uint32_t on = (cen[j] > c.threshold && cen[j] >= nb[j]) ? 1u : 0u;
-                bits |= on << (8 * j);
+                const bool lo_on = ((cand >> j) & 1u) && (below == nullptr || cen[j] >= below[j]);
+                const bool hi_on = ((cand >> (4 + j)) & 1u) && (below == nullptr || cen[4 + j] >= below[4 + j]);
+                b0 |= (lo_on ? 1u : 0u) << (8 * j);
+                b1 |= (hi_on ? 1u : 0u) << (8 * j);
             }
             if (!producer) return;
+            SHINE_CHECK(a.dbg, y >= a.ylo && y < a.yhi, kDbgFwdStore);
             uint8_t* mrow = c.mask + (int64_t)(y - a.oy) * c.mask_pitch;
             if (!E && c.mask_vec) {
-                *reinterpret_cast<uint32_t*>(mrow + (x - a.ox)) = bits;
+                *reinterpret_cast<uint2*>(mrow + (x - a.ox)) = make_uint2(b0, b1);
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (!E || cin[j]) mrow[x + j - a.ox] = (uint8_t)((bits >> (8 * j)) & 0xffu);
+                for (int j = 0; j < 8; ++j)
+                    if (!E || col_in(j)) mrow[x + j - a.ox] = (uint8_t)(((j < 4 ? b0 : b1) >> (8 * (j & 3))) & 0xffu);
             }
         };
-        auto store = [&](auto edge_tag, int y, const float R[4]) {
+        auto store = [&](auto edge_tag, int y, const float R[8]) {
             constexpr bool E = decltype(edge_tag)::value;
-            if (a.out != nullptr && producer && y >= y0 && y < y1) {
-                TO* orow = static_cast<TO*>(a.out) + (int64_t)(y - a.oy) * a.out_pitch;
+            if (out != nullptr && producer && y >= y0 && y < y1) {
+                TO* orow = out + (int64_t)(y - a.oy) * a.out_pitch;
                 if (!E && a.out_vec) {
-                    store4(orow + x, R);
+                    store8(orow + x, R);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (!E || cin[j]) orow[x + j - a.ox] = Conv<TO>::st(R[j]);
+                    for (int j = 0; j < 8; ++j)
+                        if (!E || col_in(j)) orow[x + j - a.ox] = Conv<TO>::st(R[j]);
                 }
             }
-            float r[4], r6[6], hm[4];
+            float r[8], r10[10], hm[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) r[j] = (!E || cin[j]) ? R[j] : kNegInf;
-            make_row6(r, r6);
+            for (int j = 0; j < 8; ++j) r[j] = (!E || col_in(j)) ? R[j] : kNegInf;
+            widen10<false>(r, r10, x, 0);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) hm[j] = fmaxf(fmaxf(r6[j], r6[j + 1]), r6[j + 2]);
-            if (y - 1 >= y0) {
-                float nb[4];
+            for (int j = 0; j < 8; ++j) hm[j] = max3_nan(r10[j], r10[j + 1], r10[j + 2]);
+            if (y - 1 >= y0) emit(edge_tag, y - 1, hm);
+            uint32_t nc = 0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) nb[j] = fmaxf(ha[j], hm[j]);
-                emit(edge_tag, y - 1, nb);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                ha[j] = fmaxf(hb[j], hm[j]);
+            for (int j = 0; j < 8; ++j) {
+                nc |= ((r[j] > c.threshold && r[j] >= max_nan(hb[j], hm[j])) ? 1u : 0u) << j;
                 hb[j] = hm[j];
                 cen[j] = r[j];
             }
+            cand = nc;
         };
         const std::integral_constant<bool, true> on_edge{};
         const std::integral_constant<bool, false> inside{};
-        if (edge) {
-            fwd_rows<TI, kFwdEdgeStages, true, ALIGNED>(a, P, x, ys, ye,
-                                                        [&](int y, const float R[4]) { store(on_edge, y, R); });
-        } else if constexpr (TMA) {
-            fwd_rows_bulk<TI, NS>(a, P, lane, x, ys, ye, ring, bulk,
-                                  [&](int y, const float R[4]) { store(inside, y, R); });
+        auto st_edge = [&](int y, const float R[8]) { store(on_edge, y, R); };
+        auto st_in = [&](int y, const float R[8]) { store(inside, y, R); };
+        if constexpr (SMEM) {
+            if constexpr (kBulk) {
+                if (!edge) wide_rows_bulk<TI, NS>(a, P, lane, x, ys, ye, ring0, bs, st_in);
+                else if constexpr (SHINE_WIDE_EDGE_LANES) wide_rows_edge<TI, NS>(a, P, lane, x, ys, ye, ring0, st_edge);
+                else wide_rows_pf<TI, true>(a, P, lane, x, ys, ye, st_edge);
+            } else {
+                if (edge) wide_rows_pf<TI, true>(a, P, lane, x, ys, ye, st_edge);
+                else wide_rows_pf<TI, false>(a, P, lane, x, ys, ye, st_in);
+            }
         } else {
-            fwd_rows<TI, D, false, ALIGNED>(a, P, x, ys, ye, [&](int y, const float R[4]) { store(inside, y, R); });
+            if (edge) wide_rows_elem<TI, true>(a, P, x, ys, ye, st_edge);
+            else wide_rows_elem<TI, false>(a, P, x, ys, ye, st_in);
         }
-        if (ye == y1 && !bulk.failed) {  // the region's last row: nothing below it
-            if (edge) emit(on_edge, y1 - 1, ha);
-            else emit(inside, y1 - 1, ha);
+        if (ye == y1 && !bs.failed) {  // the region's last row: nothing below it
+            if (edge) emit(on_edge, y1 - 1, static_cast<const float*>(nullptr));
+            else emit(inside, y1 - 1, static_cast<const float*>(nullptr));
         }
         lo += r1 - r0;
     }
-    if (bulk.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
+    if (bs.failed && lane == 0 && a.err != nullptr) atomicOr(a.err, 1u);
 }
 
 template <typename TI, typename TO>
 cudaError_t launch_corners_t(CornerArgs c, cudaStream_t s) {
-    constexpr int D = kFwdStages;
-    constexpr int NS = kFwdBulkStages;
+    constexpr int NS = SHINE_WIDE_BULK_STAGES;
+    constexpr bool kBulk = sizeof(TI) == 4 ? SHINE_WIDE_BULK_F32 : SHINE_WIDE_BULK_16;
     FwdArgs& a = c.f;
-    const bool tma = a.tma && a.aligned && (a.out == nullptr || a.out_vec) && c.mask_vec;
-    const size_t smem = tma ? (size_t)kFwdThreads * NS * 12 * sizeof(TI) + (kFwdThreads / 32) * NS * 8 : 0;
-    auto kern = tma ? harris_corners_kernel<TI, TO, D, true, true>
-                    : (a.aligned ? harris_corners_kernel<TI, TO, D, true, false>
-                                 : harris_corners_kernel<TI, TO, D, false, false>);
+    const bool smem_stage = a.tma;
+    const size_t smem = smem_stage && kBulk ? (size_t)(kFwdThreads / 32) * NS * (kWSegLoad * 3 * sizeof(TI) + 8) : 0;
+    auto kern = smem_stage ? harris_corners_kernel<TI, TO, true> : harris_corners_kernel<TI, TO, false>;
+    // the wide layout: segments of kWSegOut output columns, segment 0 at the storage type's origin
+    a.x0 = wide_origin<TI>();
+    a.nseg = (a.xhi - a.x0 + kWSegOut - 1) / kWSegOut;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
     if (units <= 0) return cudaSuccess;
-    if (tma) {
+    if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

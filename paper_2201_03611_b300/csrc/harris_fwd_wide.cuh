@@ -446,4 +446,114 @@ struct WideLaneStage {
     __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
 };
 
+// ---------------------------------------------------------------------------------------------
+// Row sources of the wide strip, one per staging kind: each stages the gray rows of the strip
+// (rows y0-2 .. y1+1, clamped) and runs wide_strip_core over the rows [y0, y1), handing every R
+// row to store(y, R) on every lane (the forward stores it, the corner kernel suppresses
+// non-maxima first).
+// ---------------------------------------------------------------------------------------------
+
+// Rows that are not 16-byte aligned: each lane loads its pixels of the next row element by
+// element, one row ahead.
+template <typename TI, bool EDGE, typename Store>
+__device__ __forceinline__ void wide_rows_elem(const FwdArgs& a, const Params& P, int x, int y0, int y1,
+                                               Store&& store) {
+    const int H = a.H, W = a.W;
+    const TI* img = static_cast<const TI*>(a.img);
+    int row = y0 - 2;  // image row (unclamped) of the next gray row
+    WideRaw<TI> buf;
+    wide_load<TI, false>(img, a.img_pitch, clampi(row, H), x, W, buf);
+    auto take = [&](float g10[10]) {
+        float c[8];
+        gray8<TI>(buf, c);
+        ++row;
+        wide_load<TI, false>(img, a.img_pitch, clampi(row, H), x, W, buf);
+        widen10<EDGE>(c, g10, x, W);
+    };
+    wide_strip_core<EDGE>(P, x, W, H, y0, y1, take, store, [] { return true; });
+}
+
+// 16-byte aligned rows staged in registers: each lane loads its 8 pixels of the next row with
+// 16-byte loads one row ahead (element by element where a lane straddles the image edge), and
+// lane 0 prefetches the warp's span of the row kWidePfRows ahead into L2 with one bulk prefetch,
+// so the register loads hit L2. Nothing waits on the prefetch.
+template <typename TI, bool EDGE, typename Store>
+__device__ __forceinline__ void wide_rows_pf(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                             Store&& store) {
+    constexpr int K = kWidePfRows;
+    const int H = a.H, W = a.W;
+    const TI* img = static_cast<const TI*>(a.img);
+    // the warp's 256 staged pixels clipped to the image, in whole 16-byte chunks
+    const int xs = x - kWCols * lane;
+    const int plo = xs < 0 ? 0 : xs, phi = xs + kWSegLoad < W ? xs + kWSegLoad : W;
+    const uint32_t pbytes = (uint32_t)((phi - plo) * 3 * (int)sizeof(TI)) & ~15u;
+    const char* prow = reinterpret_cast<const char*>(img + (int64_t)plo * 3);
+    const int64_t pitch_b = a.img_pitch * (int64_t)sizeof(TI);
+    SHINE_CHECK(a.dbg, pbytes <= (uint32_t)((phi - plo) * 3 * (int)sizeof(TI)), kDbgFwdStage);
+    if constexpr (!EDGE) SHINE_CHECK(a.dbg, x >= 0 && x + kWCols <= W, kDbgFwdLoad);
+    int pr = y0 - 2;  // next row to prefetch (unclamped)
+    const uint32_t lead = lane == 0 && pbytes != 0;
+    auto prefetch_next = [&]() {
+        prefetch_l2_pred(lead && pr >= 0 && pr < H, prow + (int64_t)(pr < 0 ? 0 : pr) * pitch_b, pbytes);
+        ++pr;
+    };
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) prefetch_next();
+    int row = y0 - 2;  // image row (unclamped) of the next gray row
+    WideRaw<TI> buf;
+    wide_load<TI, true, !EDGE>(img, a.img_pitch, clampi(row, H), x, W, buf);
+    auto take = [&](float g10[10]) {
+        float c[8];
+        gray8<TI>(buf, c);
+        ++row;
+        wide_load<TI, true, !EDGE>(img, a.img_pitch, clampi(row, H), x, W, buf);  // one row ahead
+        prefetch_next();
+        widen10<EDGE>(c, g10, x, W);
+    };
+    wide_strip_core<EDGE>(P, x, W, H, y0, y1, take, store, [] { return true; });
+}
+
+// An edge segment of a 16-byte aligned image, staged per lane by cp.async.
+template <typename TI, int NS, typename Store>
+__device__ __forceinline__ void wide_rows_edge(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                               uint32_t ring0, Store&& store) {
+    const int H = a.H, W = a.W;
+    const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    SHINE_CHECK(a.dbg, smem_in(ring0, NS * WideLaneStage<TI, NS>::kSlotBytes), kDbgSmem);
+    WideLaneStage<TI, NS> src(static_cast<const TI*>(a.img), a.img_pitch, x, W, H, ring0, lane, y0 - 2, n);
+    // a lane whose columns all lie outside the row copies nothing (zero-fill only)
+    SHINE_CHECK(a.dbg, src.valid_bytes == 0 || (x >= 0 && (x + kWCols <= W ? kWCols : W - x) * 3 * (int)sizeof(TI) ==
+                                                              src.valid_bytes),
+                kDbgFwdStage);
+    auto take = [&](float g10[10]) {
+        WideRaw<TI> r;
+        src.take_raw(r);
+        float c[8];
+        gray8<TI>(r, c);
+        widen10<true>(c, g10, x, W);
+    };
+    wide_strip_core<true>(P, x, W, H, y0, y1, take, store, [] { return true; });
+    src.finish();
+}
+
+// An interior segment of a 16-byte aligned image, staged by bulk copies.
+template <typename TI, int NS, typename Store>
+__device__ __forceinline__ void wide_rows_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
+                                               uint32_t ring0, WideBulkState& bs, Store&& store) {
+    const int H = a.H;
+    const int n = (y1 == H ? y1 - y0 + 3 : y1 - y0 + 4);  // gray rows y0-2 .. min(y1+1, H)
+    SHINE_CHECK(a.dbg, x - kWCols * lane >= 0 && x - kWCols * lane + kWSegLoad <= a.W, kDbgFwdStage);
+    SHINE_CHECK(a.dbg, smem_in(ring0, NS * WideBulk<TI, NS>::kBytes), kDbgSmem);
+    WideBulk<TI, NS> src(bs, static_cast<const TI*>(a.img), a.img_pitch, x - kWCols * lane, ring0, lane, y0 - 2, n, H);
+    auto take = [&](float g10[10]) {
+        WideRaw<TI> r;
+        src.take_raw(r);
+        float c[8];
+        gray8<TI>(r, c);
+        widen10<false>(c, g10, x, 0);
+    };
+    wide_strip_core<false>(P, x, a.W, H, y0, y1, take, store, [&] { return !bs.failed; });
+    src.finish();
+}
+
 }  // namespace shine

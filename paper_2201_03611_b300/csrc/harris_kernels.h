@@ -201,8 +201,7 @@ struct FwdArgs : Geometry {
     const float* wx;
     const float* wy;
     int aligned;  // image rows can be staged with 16 / 8-byte copies
-    int out_vec;  // output rows can be written with vector stores: 16-byte aligned rows for the
-                  // forward kernel, 4-element aligned rows for the corner kernel
+    int out_vec;  // output rows can be written with 16-byte vector stores
     int tma;      // interior segments may use bulk (TMA) staging (16-byte aligned rows)
     unsigned int* err;  // nonzero after a bounded wait gave up (nullable)
 };
@@ -214,7 +213,7 @@ struct CornerArgs {
     uint8_t* mask;
     int64_t mask_pitch;  // bytes
     float threshold;
-    int mask_vec;        // mask rows can be written 4 bytes at a time
+    int mask_vec;        // mask rows can be written 8 bytes at a time
 };
 
 // The backward pass always covers every image pixel (its output is d img, H x W), so its
@@ -291,6 +290,9 @@ static_assert(SHINE_WIDE_ORIGIN_F32 % 8 == 0 && SHINE_WIDE_ORIGIN_F32 > -240 && 
               "wide segment spans must start on 8-pixel boundaries");
 // Shared-memory slots of the forward's bulk staging ring (measured on 8192^2 float32: 4 slots
 // 0.173 ms, 6 slots 0.185 ms).
+#ifndef SHINE_WIDE_CORNERS_MIN_BLOCKS
+#define SHINE_WIDE_CORNERS_MIN_BLOCKS 3  // the corner kernel: resident 128-thread CTAs per SM (registers)
+#endif
 #ifndef SHINE_WIDE_BULK_STAGES
 #define SHINE_WIDE_BULK_STAGES 4
 #endif

@@ -99,3 +99,17 @@ def test_full_size_salt_8192(shine):
     got = mask.cpu().numpy()
     assert np.array_equal(got, C.nms(r32, thr))
     assert 0 < got.sum() < got.size // 10
+
+
+def test_nan_in_R(shine):
+    """NaN pixels make NaN patches in R: a NaN is never a corner and, since no value is >= NaN,
+    neither is a pixel with a NaN neighbour (the definition, applied to the kernel's own R)."""
+    img = wl.random_image(90, 300, seed=9).cuda()
+    for y, x, ch in ((40, 100, 0), (10, 250, 2), (89, 0, 1), (0, 299, 0)):
+        img[y, x, ch] = float("nan")
+    k, wx, wy = _params(9)
+    r32 = shine.pipeline_fwd(img, k, wx, wy, "clamp").cpu().numpy()
+    assert np.isnan(r32).any() and np.isfinite(r32).any()
+    thr = float(np.quantile(r32[np.isfinite(r32)], 0.6))
+    mask, _ = shine.corners(img, k, wx, wy, thr, "clamp")
+    assert np.array_equal(mask.cpu().numpy(), C.nms(r32, thr))

@@ -56,6 +56,11 @@ def test_nan_is_never_a_corner_and_constant_field_is_all_corners():
     R[1, 1] = np.nan
     m = both(R, 0.0)
     assert m[1, 1] == 0
+    # no value is >= NaN: every pixel with the NaN among its neighbours is no corner either
+    assert m.sum() == 0
+    R = np.full((3, 5), 1.0, dtype=np.float32)
+    R[1, 0] = np.nan
+    assert both(R, 0.0)[:, 2:].all() and both(R, 0.0)[:, :2].sum() == 0
 
 
 @pytest.mark.parametrize("seed", range(6))
