@@ -54,8 +54,8 @@ def _peaks() -> tuple[float, str]:
 
 
 # The sources that decide the code of the forward and adjoint kernels the bench times.
-KERNEL_SOURCES = ("api.cu", "harris_common.cuh", "harris_kernels.h", "harris_fwd_strip.cuh", "harris_fwd_wide.cuh",
-                  "harris_fwd.cu", "harris_bwd_strip.cuh", "harris_adj_wide.cuh", "harris_bwd.cu")
+KERNEL_SOURCES = ("api.cu", "harris_common.cuh", "harris_kernels.h", "harris_fwd_wide.cuh", "harris_fwd.cu",
+                  "harris_bwd_strip.cuh", "harris_adj_wide.cuh", "harris_bwd.cu")
 
 
 def kernel_source_hash() -> str:

@@ -192,17 +192,7 @@ struct BulkGray {
     }
 };
 
-// The forward's rows y0 .. y1-1 on an interior segment, staged by BulkGray.
-template <typename TI, int NS, typename Store>
-__device__ __forceinline__ void fwd_rows_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
-                                              const TI* ring, FwdBulk& bulk, Store&& store) {
-    BulkGray<TI, NS> src(a, bulk, ring, lane, x, y0 - 2, y1 - y0 + 4);  // gray rows y0-2 .. y1+1
-    fwd_strip_core<false, 1>(P, x, 0, a.H, y0, y1, [&](int, int, float g6[6]) { src.take(g6); }, store,
-                             [&] { return !bulk.failed; });
-    src.finish();
-}
-
-// Forward strips that write R: any segment (register staging) ...
+// Forward strip that writes R (register staging; any segment): the batched forward-only mode.
 template <typename TI, typename TO, int D, bool EDGE, bool ALIGNED>
 __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1) {
     TO* out = static_cast<TO*>(a.out);
@@ -219,19 +209,6 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs& a, const Params& P, int
                 if (c >= a.xlo && c < a.xhi) orow[c - a.ox] = Conv<TO>::st(R[j]);
             }
         }
-    });
-}
-
-// ... and interior segments staged by bulk copies (R stored with vector stores).
-template <typename TI, typename TO, int NS>
-__device__ __forceinline__ void fwd_strip_bulk(const FwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
-                                               const TI* ring, FwdBulk& bulk) {
-    TO* orow = static_cast<TO*>(a.out) + (int64_t)y0 * a.out_pitch + x;  // interior: no output offset
-    const int64_t opitch = a.out_pitch;
-    const bool producer = lane >= 1 && lane <= 30;
-    fwd_rows_bulk<TI, NS>(a, P, lane, x, y0, y1, ring, bulk, [&](int, const float R[4]) {
-        if (producer) store4(orow, R);
-        orow += opitch;
     });
 }
 
