@@ -333,7 +333,10 @@ struct WAdjLanes {
 // The strip: rows y0 .. y1-1 of the segment whose lane-1 column is x + 8 (x = the lane's first
 // column). The strip's parameter-cotangent terms are added into the lane's shared-memory sums.
 // ---------------------------------------------------------------------------------------------
-template <typename TI, bool EDGE, bool BULK, typename Src>
+// WITH_R: also store R (computed anyway in B1) at the rows this warp owns, for the fused
+// forward+backward pass (CLAMP: the output has the image's geometry); a.rout_vec allows 16-byte
+// stores of a lane's 8 values.
+template <typename TI, bool EDGE, bool BULK, bool WITH_R, typename Src>
 __device__ __forceinline__ void wide_adj_strip(const BwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
                                                Src& src, const WRings& rg, const bool* failed) {
     const int H = a.H, W = a.W;
@@ -426,6 +429,24 @@ __device__ __forceinline__ void wide_adj_strip(const BwdArgs& a, const Params& P
             hbox8<EDGE>(vxy, Sxy, x, W);
         }
         const bool own_row = FAST || (sr >= y0 && sr < y1);
+        if constexpr (WITH_R) {
+            // A5 at row sr, bit-identical to the forward's R (same sums in the same order)
+            if (own_row && producer) {
+                float R[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) R[j] = response(S2[j].x, Sxy[j], S2[j].y, P.kappa);
+                SHINE_CHECK(a.dbg, sr >= 0 && sr < H && (!full || !a.rout_vec || (x >= 0 && x + kWCols <= W)),
+                            kDbgBwdStore);
+                TI* orow = static_cast<TI*>(a.rout) + (int64_t)sr * a.rout_pitch;
+                if (full && a.rout_vec) {
+                    store8(orow + x, R);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (cin[j]) orow[x + j] = Conv<TI>::st(R[j]);
+                }
+            }
+        }
         // B2: gS at row r-2 and the d kappa terms.
         float2 gsn[8];
         float gqn[8];

@@ -100,7 +100,7 @@ constexpr size_t wide_adj_smem(int ns) {
     return (size_t)(kBwdThreads / 32) * ns * (WSlot<TI, TG>::kBytes + 8) + (size_t)(kBwdThreads / 32) * kWRingBytes;
 }
 
-template <typename TI, typename TG, int NS>
+template <typename TI, typename TG, int NS, bool WITH_R>
 __global__ void __launch_bounds__(kBwdThreads) harris_bwd_wide_kernel(BwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int kWarps = kBwdThreads / 32;
@@ -146,12 +146,12 @@ __global__ void __launch_bounds__(kBwdThreads) harris_bwd_wide_kernel(BwdArgs a)
                                    (x >= 0 && x * 3 * (int)sizeof(TI) + src.vbytes_img <= 3 * a.W * (int)sizeof(TI) &&
                                     x * (int)sizeof(TG) + src.vbytes_cot <= a.gwo * (int)sizeof(TG)),
                         kDbgBwdStage);
-            wide_adj_strip<TI, true, false>(a, P, lane, x, y0, y1, src, rg, nullptr);
+            wide_adj_strip<TI, true, false, WITH_R>(a, P, lane, x, y0, y1, src, rg, nullptr);
         } else {
             SHINE_CHECK(a.dbg, xb - kWCols >= 0 && xb - kWCols + kWSegLoad <= a.W && xb - kWCols + kWSegLoad <= a.gwo,
                         kDbgBwdStage);
             WAdjBulk<TI, TG, NS> src(bulk, a, ring0, lane, xb - kWCols, y0 - 4, n);
-            wide_adj_strip<TI, false, true>(a, P, lane, x, y0, y1, src, rg, &bulk.failed);
+            wide_adj_strip<TI, false, true, WITH_R>(a, P, lane, x, y0, y1, src, rg, &bulk.failed);
         }
         lo += r1 - r0;
     }
@@ -183,7 +183,10 @@ template <typename TI, typename TG>
 cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
     constexpr int NS = sizeof(TI) == 4 ? SHINE_WIDE_BWD_STAGES_F32 : SHINE_WIDE_BWD_STAGES;
     const size_t smem = wide_adj_smem<TI, TG>(NS);
-    auto kern = harris_bwd_wide_kernel<TI, TG, NS>;
+    auto kern = a.rout != nullptr ? harris_bwd_wide_kernel<TI, TG, NS, true> : harris_bwd_wide_kernel<TI, TG, NS, false>;
+    // R of the fused pass: 16-byte stores of a lane's eight values need 16-byte aligned rows
+    a.rout_vec = a.rout_vec && reinterpret_cast<uintptr_t>(a.rout) % 16 == 0 &&
+                 ((size_t)a.rout_pitch * sizeof(TI)) % 16 == 0;
     a.x0 = SHINE_WIDE_BWD_ORIGIN;
     a.nseg = (a.xhi - a.x0 + kWSegOut - 1) / kWSegOut;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;
@@ -201,12 +204,13 @@ cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* use
 
 template <typename TI, typename TG>
 cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
-    // 16-bit CLAMP images with 16-byte aligned image and cotangent rows (a.tma), adjoint only: the
-    // wide kernel (measured on 8192^2: bf16 0.409 -> 0.388 ms, fp16 0.440 -> 0.410 ms; float32
+    // 16-bit CLAMP images with 16-byte aligned image and cotangent rows (a.tma): the wide kernel,
+    // for the adjoint (measured on 8192^2: bf16 0.409 -> 0.388 ms, fp16 0.440 -> 0.410 ms; float32
     // 0.413 -> 0.478 ms, where its 96-byte lane pieces meet 2-way bank conflicts, so float32
-    // images stay on the four-column kernel)
+    // images stay on the four-column kernel) and for the fused pass
     if constexpr (SHINE_WIDE_BWD && (sizeof(TI) == 2 || SHINE_WIDE_BWD_F32)) {
-        if (a.tma && !a.valid && a.rout == nullptr) return launch_bwd_wide_t<TI, TG>(a, max_warps, s, used);
+        if (a.tma && !a.valid && (a.rout == nullptr || SHINE_WIDE_BWD_FUSED))
+            return launch_bwd_wide_t<TI, TG>(a, max_warps, s, used);
     }
     // ring depth: the adjoint alone takes bwd_stages<TI>(), the fused forward+adjoint (which also
     // stores R) the default depth (measured: float32 fused 0.486 ms at 8 rows, 0.494 at 6)

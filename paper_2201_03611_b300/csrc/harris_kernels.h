@@ -44,6 +44,9 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_WIDE_BWD_STAGES_F32
 #define SHINE_WIDE_BWD_STAGES_F32 3  // its staging ring for float32 images (8 warps x 28 KB)
 #endif
+#ifndef SHINE_WIDE_BWD_FUSED
+#define SHINE_WIDE_BWD_FUSED 1    // the fused forward+backward pass of those images takes it too
+#endif
 #ifndef SHINE_WIDE_BWD_SWAP_PAIRS
 #define SHINE_WIDE_BWD_SWAP_PAIRS 1  // conflict-free float32 reads of the staged pieces
 #endif

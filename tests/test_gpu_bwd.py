@@ -132,9 +132,12 @@ def test_bwd_deterministic(shine):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("shape,border", [((37, 250), "clamp"), ((70, 245), "valid"), ((3, 3), "clamp")])
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("shape,border", [((37, 250), "clamp"), ((70, 245), "valid"), ((3, 3), "clamp"),
+                                          ((67, 256), "clamp"), ((130, 1000), "clamp")])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_fused_equals_separate(shine, shape, border, dtype):
+    """The fused pass gives the forward's R and the adjoint's cotangents bit for bit (16-byte
+    aligned 16-bit rows -- 256 and 1000 columns -- take the eight-column kernel for both)."""
     h, w = shape
     img = wl.random_image(h, w, seed=8).to(dtype).cuda()
     ho, wo = shine.output_shape(h, w, border)
