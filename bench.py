@@ -376,7 +376,8 @@ def _fma_lane_cycles_per_s() -> float:
 
 def precision_extra(S, device, size: int, reps: int) -> dict:
     """The precision workload: bf16 / fp16 storage (float32 arithmetic), forward + backward of the
-    unsalted size x size image, timed like the main step. Besides the fraction of the HBM copy
+    unsalted size x size image, timed like the main step, and the fused single pass (16 bytes per
+    pixel: image 6 + cotangent 2 in, R 2 + d img 6 out). Besides the fraction of the HBM copy
     rate, each pass reports the fraction of the float32 pipe's peak its arithmetic needs (16-bit
     storage halves the bytes, not the arithmetic, so these passes are bound by the FMA pipe and
     instruction issue). Its errors against the oracle (on the
@@ -398,11 +399,14 @@ def precision_extra(S, device, size: int, reps: int) -> dict:
         stream = torch.cuda.current_stream(device)
         fwd = lambda: S.pipeline_fwd(img, k, dwx, dwy, "clamp", out=o)
         bwd = lambda: S.pipeline_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, grad_img=gi)
+        # the cotangent known before the forward pass (as in the fused_step extra): one launch
+        fused = lambda: S.pipeline_fwd_bwd(img, g, k, dwx, dwy, "clamp", workspace=ws, out=o, grad_img=gi)
         for _ in range(3):
-            fwd(); bwd()
+            fwd(); bwd(); fused()
         torch.cuda.synchronize()
         t_f = _time_ms(fwd, reps, stream)
         t_b = _time_ms(bwd, reps, stream)
+        t_fb = _time_ms(fused, reps, stream)
         px = size * size
         fma_peak = _fma_lane_cycles_per_s()
         out[name] = {
@@ -411,6 +415,8 @@ def precision_extra(S, device, size: int, reps: int) -> dict:
             "bwd_frac_of_measured_hbm": 14 * px / (t_b * 1e-3) / 1e9 / _peaks()[0],
             "fwd_frac_of_fma_pipe": FMA_LANE_CYCLES_PER_PX["fwd"] * px / (t_f * 1e-3) / fma_peak,
             "bwd_frac_of_fma_pipe": FMA_LANE_CYCLES_PER_PX["bwd"] * px / (t_b * 1e-3) / fma_peak,
+            "fused_ms": t_fb, "fused_gpix_s": px / (t_fb * 1e-3) / 1e9,
+            "fused_frac_of_measured_hbm": 16 * px / (t_fb * 1e-3) / 1e9 / _peaks()[0],
             "errors": "tests/test_gpu_precision.py (sampled outputs against the FP64 oracle)"}
         del img, g, o, gi, ws
     return out
