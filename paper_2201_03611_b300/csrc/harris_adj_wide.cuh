@@ -333,9 +333,9 @@ struct WAdjLanes {
 // The strip: rows y0 .. y1-1 of the segment whose lane-1 column is x + 8 (x = the lane's first
 // column). The strip's parameter-cotangent terms are added into the lane's shared-memory sums.
 // ---------------------------------------------------------------------------------------------
-// WITH_R: also store R (computed anyway in B1) at the rows this warp owns, for the fused
-// forward+backward pass (CLAMP: the output has the image's geometry); a.rout_vec allows 16-byte
-// stores of a lane's 8 values.
+// WITH_R: also store R (computed anyway in B1) at the rows this warp owns into a.rout when it is
+// given, for the fused forward+backward pass (CLAMP: the output has the image's geometry);
+// a.rout_vec allows 16-byte stores of a lane's 8 values.
 template <typename TI, bool EDGE, bool BULK, bool WITH_R, typename Src>
 __device__ __forceinline__ void wide_adj_strip(const BwdArgs& a, const Params& P, int lane, int x, int y0, int y1,
                                                Src& src, const WRings& rg, const bool* failed) {
@@ -431,7 +431,7 @@ __device__ __forceinline__ void wide_adj_strip(const BwdArgs& a, const Params& P
         const bool own_row = FAST || (sr >= y0 && sr < y1);
         if constexpr (WITH_R) {
             // A5 at row sr, bit-identical to the forward's R (same sums in the same order)
-            if (own_row && producer) {
+            if (own_row && producer && a.rout != nullptr) {
                 float R[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) R[j] = response(S2[j].x, Sxy[j], S2[j].y, P.kappa);

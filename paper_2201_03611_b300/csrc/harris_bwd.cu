@@ -184,9 +184,11 @@ cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* use
     constexpr int NS = sizeof(TI) == 4 ? SHINE_WIDE_BWD_STAGES_F32 : SHINE_WIDE_BWD_STAGES;
     const size_t smem = wide_adj_smem<TI, TG>(NS);
     auto kern = a.rout != nullptr ? harris_bwd_wide_kernel<TI, TG, NS, true> : harris_bwd_wide_kernel<TI, TG, NS, false>;
-    // R of the fused pass: 16-byte stores of a lane's eight values need 16-byte aligned rows
+    // a lane's eight values of R and 24 of d img go out in 16-byte stores: 16-byte aligned rows
     a.rout_vec = a.rout_vec && reinterpret_cast<uintptr_t>(a.rout) % 16 == 0 &&
                  ((size_t)a.rout_pitch * sizeof(TI)) % 16 == 0;
+    a.gimg_vec = a.gimg_vec && reinterpret_cast<uintptr_t>(a.gimg) % 16 == 0 &&
+                 ((size_t)a.gimg_pitch * sizeof(TI)) % 16 == 0;
     a.x0 = SHINE_WIDE_BWD_ORIGIN;
     a.nseg = (a.xhi - a.x0 + kWSegOut - 1) / kWSegOut;
     const int64_t units = (int64_t)(a.yhi - a.ylo) * a.nseg;

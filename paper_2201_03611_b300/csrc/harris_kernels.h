@@ -240,7 +240,8 @@ struct BwdArgs : Geometry {
     int tma;           // interior segments may use bulk (TMA) staging
     int aligned;       // image staging
     int g_aligned;     // cotangent staging (CLAMP with aligned pointer and pitch)
-    int gimg_vec;      // d img rows can be written with 16 / 8-byte stores
+    int gimg_vec;      // d img rows can be written with vector stores (16 / 8-byte aligned rows; the
+                       // eight-column kernel needs 16 for every storage type)
     void* rout;        // fused forward output R (nullable; storage type of the image)
     int64_t rout_pitch;
     int rout_vec;      // R rows can be written with 16 / 8-byte stores

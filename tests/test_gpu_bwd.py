@@ -280,3 +280,24 @@ def test_zero_cotangent_gives_exact_zeros(shine, dtype):
         k, dwx, dwy = U.dev_params(0.04, *wl.random_weights(3))
         for t in shine.pipeline_bwd(img, g, k, dwx, dwy, "clamp"):
             assert torch.count_nonzero(t) == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_wide_path_with_8_byte_aligned_outputs(shine, dtype):
+    """16-byte aligned image and cotangent rows take the eight-column kernel; d img (and R) rows
+    that are only 8-byte aligned (260 columns: 1560-byte rows) are then written element by
+    element. Same bits as the four-column kernel on an unpadded image."""
+    h, w = 70, 260
+    img = wl.random_image(h, w, seed=41).to(dtype)
+    g = wl.random_cotangent(h, w, seed=42).to(dtype)
+    k, dwx, dwy = U.dev_params(0.05, *wl.random_weights(41))
+    img_a, g_a = wl.to_device(wl.padded(img), "cuda"), wl.to_device(wl.padded(g), "cuda")
+    assert img_a.stride(0) * 2 % 16 == 0 and g_a.stride(0) * 2 % 16 == 0
+    gi8 = torch.empty(h, w, 3, dtype=dtype, device="cuda")      # 1560-byte rows
+    r8 = torch.empty(h, w, dtype=dtype, device="cuda")          # 520-byte rows
+    gi_ref, *p_ref = shine.pipeline_bwd(U.padded_image(img.cuda(), 1), g.cuda(), k, dwx, dwy, "clamp")
+    gi_w = shine.pipeline_bwd(img_a, g_a, k, dwx, dwy, "clamp", grad_img=gi8)[0]
+    assert torch.equal(gi_w, gi_ref)
+    fused = shine.pipeline_fwd_bwd(img_a, g_a, k, dwx, dwy, "clamp", out=r8, grad_img=torch.empty_like(gi8))
+    assert torch.equal(fused[0], shine.pipeline_fwd(img.cuda(), k, dwx, dwy, "clamp"))
+    assert torch.equal(fused[1], gi_ref)
