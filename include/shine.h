@@ -117,7 +117,11 @@ SHINE_API shine_status shine_pipeline_bwd_workspace(int64_t H, int64_t W, shine_
  *   workspace  at least shine_pipeline_bwd_workspace() bytes of device memory, 16-byte
  *              aligned; its contents are scratch (per-tile partial sums)
  * The parameter cotangents are reduced in a fixed order in float64, so repeated calls give
- * bit-identical results.
+ * bit-identical results. Kernel choice: 16-bit CLAMP images whose image and cotangent rows are
+ * 16-byte aligned take the eight-columns-per-lane kernel from 2^25 pixels on (the environment
+ * variable SHINE_WIDE_BWD_MIN_PIXELS, read at every call, moves that bound); R and d img are
+ * bit-identical either way, the parameter cotangents are the same terms summed over another
+ * partition. The same holds for shine_pipeline_fwd_bwd.
  */
 SHINE_API shine_status shine_pipeline_bwd(const void* img, int64_t H, int64_t W, int64_t img_pitch,
                                 shine_dtype dt, shine_border border, const float* kappa,

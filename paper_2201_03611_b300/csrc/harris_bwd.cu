@@ -23,6 +23,7 @@
 // Parameter cotangents are accumulated per lane in float32, reduced per warp in float64 and
 // summed in a fixed order by the finalize kernel, so every run gives the same bits.
 #include <algorithm>
+#include <cstdlib>
 
 #include "harris_adj_wide.cuh"
 #include "harris_bwd_strip.cuh"
@@ -204,14 +205,30 @@ cudaError_t launch_bwd_wide_t(BwdArgs a, int max_warps, cudaStream_t s, int* use
     return cudaPeekAtLastError();
 }
 
+// Image size (pixels) from which 16-bit CLAMP images take the eight-column adjoint: the
+// environment variable SHINE_WIDE_BWD_MIN_PIXELS when set (read at every call, so that a test can
+// reach either kernel on the same image), else SHINE_WIDE_BWD_MIN_PIXELS of the build.
+int64_t wide_bwd_min_pixels() {
+    if (const char* v = std::getenv("SHINE_WIDE_BWD_MIN_PIXELS")) {
+        char* end = nullptr;
+        const long long n = std::strtoll(v, &end, 10);
+        if (end != v && *end == '\0' && n >= 0) return (int64_t)n;
+    }
+    return SHINE_WIDE_BWD_MIN_PIXELS;
+}
+
 template <typename TI, typename TG>
 cudaError_t launch_bwd_t(BwdArgs a, int max_warps, cudaStream_t s, int* used) {
     // 16-bit CLAMP images with 16-byte aligned image and cotangent rows (a.tma): the wide kernel,
     // for the adjoint (measured on 8192^2: bf16 0.409 -> 0.388 ms, fp16 0.440 -> 0.410 ms; float32
     // 0.413 -> 0.478 ms, where its 96-byte lane pieces meet 2-way bank conflicts, so float32
-    // images stay on the four-column kernel) and for the fused pass
+    // images stay on the four-column kernel) and for the fused pass. Smaller images keep the
+    // four-column kernel: with one resident wave the wide strips are half as long, and their
+    // fixed cost per strip wins (bf16, adjoint / fused, us: 4096^2 129 / 152 four-column against
+    // 140 / 162 wide, 2048^2 56 / 61 against 73 / 84; 8192^2 407 / 500 against 377 / 425)
     if constexpr (SHINE_WIDE_BWD && (sizeof(TI) == 2 || SHINE_WIDE_BWD_F32)) {
-        if (a.tma && !a.valid && (a.rout == nullptr || SHINE_WIDE_BWD_FUSED))
+        if (a.tma && !a.valid && (a.rout == nullptr || SHINE_WIDE_BWD_FUSED) &&
+            (int64_t)a.H * a.W >= wide_bwd_min_pixels())
             return launch_bwd_wide_t<TI, TG>(a, max_warps, s, used);
     }
     // ring depth: the adjoint alone takes bwd_stages<TI>(), the fused forward+adjoint (which also

@@ -47,6 +47,9 @@ constexpr int kSegOut = (kLanes - 2) * kCols;  // 120 computed columns per warp 
 #ifndef SHINE_WIDE_BWD_FUSED
 #define SHINE_WIDE_BWD_FUSED 1    // the fused forward+backward pass of those images takes it too
 #endif
+#ifndef SHINE_WIDE_BWD_MIN_PIXELS
+#define SHINE_WIDE_BWD_MIN_PIXELS (int64_t(1) << 25)  // smaller images keep the four-column adjoint
+#endif
 #ifndef SHINE_WIDE_BWD_SWAP_PAIRS
 #define SHINE_WIDE_BWD_SWAP_PAIRS 1  // conflict-free float32 reads of the staged pieces
 #endif

@@ -22,6 +22,13 @@ def shine():
     return S
 
 
+@pytest.fixture
+def wide_adjoint(monkeypatch):
+    """16-bit CLAMP images with 16-byte aligned rows take the eight-column adjoint at any size
+    (by default only from 2^25 pixels on, where it is the faster one)."""
+    monkeypatch.setenv("SHINE_WIDE_BWD_MIN_PIXELS", "0")
+
+
 def _run_bwd(shine, img, g, kappa, wx, wy, border, **kw):
     k, dwx, dwy = U.dev_params(kappa, wx, wy)
     return shine.pipeline_bwd(img.cuda(), g.cuda(), k, dwx, dwy, border, **kw)
@@ -135,9 +142,13 @@ def test_bwd_deterministic(shine):
 @pytest.mark.parametrize("shape,border", [((37, 250), "clamp"), ((70, 245), "valid"), ((3, 3), "clamp"),
                                           ((67, 256), "clamp"), ((130, 1000), "clamp")])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
-def test_fused_equals_separate(shine, shape, border, dtype):
-    """The fused pass gives the forward's R and the adjoint's cotangents bit for bit (16-byte
-    aligned 16-bit rows -- 256 and 1000 columns -- take the eight-column kernel for both)."""
+@pytest.mark.parametrize("wide", [False, True])
+def test_fused_equals_separate(shine, shape, border, dtype, wide, monkeypatch):
+    """The fused pass gives the forward's R and the adjoint's cotangents bit for bit (with the
+    eight-column kernel allowed at any size, 16-byte aligned 16-bit rows -- 256 and 1000 columns --
+    take it for both)."""
+    if wide:
+        monkeypatch.setenv("SHINE_WIDE_BWD_MIN_PIXELS", "0")
     h, w = shape
     img = wl.random_image(h, w, seed=8).to(dtype).cuda()
     ho, wo = shine.output_shape(h, w, border)
@@ -231,7 +242,7 @@ def test_host_pipeline_matches_device_calls(shine, shape, border, dtype, nbands)
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("shape", [(1, 8), (3, 16), (9, 248), (37, 256), (64, 496), (130, 512), (300, 264),
                                    (5, 1024), (257, 744)])
-def test_bwd_16bit_wide_path(shine, dtype, shape):
+def test_bwd_16bit_wide_path(shine, dtype, shape, wide_adjoint):
     """16-bit CLAMP images whose rows are 16-byte aligned (W a multiple of 8) take the eight-
     columns-per-lane adjoint: interior segments bulk-staged, edge segments staged per lane, ragged
     column and row tails. d img must equal, bit for bit, the four-column adjoint's (reached through
@@ -253,7 +264,7 @@ def test_bwd_16bit_wide_path(shine, dtype, shape):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("shape", [(3, 70000), (70001, 8), (2, 65536), (5, 1), (1, 131072)])
-def test_extreme_aspect_ratios(shine, dtype, shape):
+def test_extreme_aspect_ratios(shine, dtype, shape, wide_adjoint):
     """Very wide and very tall images (hundreds of column segments of a few rows each, or one
     segment of tens of thousands of rows): forward and adjoint against the oracle."""
     h, w = shape
@@ -272,7 +283,7 @@ def test_extreme_aspect_ratios(shine, dtype, shape):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_zero_cotangent_gives_exact_zeros(shine, dtype):
+def test_zero_cotangent_gives_exact_zeros(shine, dtype, wide_adjoint):
     """A zero cotangent: every cotangent output is exactly zero (both adjoint kernels)."""
     for w in (256, 250):  # aligned 16-bit rows (eight-column kernel) and not
         img = wl.random_image(97, w, seed=w).to(dtype).cuda()
@@ -283,7 +294,7 @@ def test_zero_cotangent_gives_exact_zeros(shine, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-def test_wide_path_with_8_byte_aligned_outputs(shine, dtype):
+def test_wide_path_with_8_byte_aligned_outputs(shine, dtype, wide_adjoint):
     """16-byte aligned image and cotangent rows take the eight-column kernel; d img (and R) rows
     that are only 8-byte aligned (260 columns: 1560-byte rows) are then written element by
     element. Same bits as the four-column kernel on an unpadded image."""

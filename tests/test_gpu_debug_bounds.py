@@ -3,8 +3,9 @@ checker, which this pool does not offer. Its Harris kernels check the row and co
 every global load, store and copy and of their shared-memory staging and record violations in a
 device word instead of trapping. Here it runs the forward, the adjoint (all staging paths, both
 adjoint layouts), the fused pass, the host-buffer pipeline and a batch under two schedules on
-ragged shapes in a child process, which must report no violation and the same results, bit for
-bit, as the release build in this process."""
+ragged shapes in a child process (with the eight-column adjoint allowed at every size), which
+must report no violation and the same results, bit for bit, as the release build in this
+process."""
 import json
 import os
 import subprocess
@@ -88,7 +89,8 @@ def test_debug_build_reports_no_violation_and_release_results(tmp_path):
     if not os.path.exists(DEBUG_LIB):
         pytest.fail("libshine_debug.so is not built (python -m paper_2201_03611_b300.build --debug)")
     import paper_2201_03611_b300 as S
-    env = dict(os.environ, SHINE_LIBRARY=DEBUG_LIB)
+    # the eight-column adjoint at every size, so that the small shapes reach it too
+    env = dict(os.environ, SHINE_LIBRARY=DEBUG_LIB, SHINE_WIDE_BWD_MIN_PIXELS="0")
     script = CHILD.format(root=ROOT, shapes=SHAPES, tmp=str(tmp_path))
     p = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stderr[-3000:]
