@@ -76,3 +76,22 @@ def test_precision_workload_errors(shine, name):
     assert report["R_vs_oracle_on_quantised_input"]["normwise_max"] <= U.TOL_16
     assert report["R_f32_output_vs_oracle_on_quantised_input"]["normwise_max"] <= U.TOL_F32
     assert report["dimg_vs_oracle_on_quantised_inputs"]["normwise_max"] <= U.TOL_16
+
+
+@pytest.mark.parametrize("name", ["bf16", "f16"])
+def test_precision_workload_fused_pass(shine, name):
+    """The fused single pass on the full precision workload, as the benchmark times it (the
+    eight-column kernel, which 16-bit images of this size take): R equals the forward's and
+    d img and the parameter cotangents equal the separate adjoint's, bit for bit."""
+    dt = wl.storage_dtype(name)
+    img = wl.random_image(SIZE, SIZE, seed=0).to(dt).cuda()
+    g = wl.random_cotangent(SIZE, SIZE, seed=1).to(dt).cuda()
+    wx, wy = wl.sobel_weights()
+    k, dwx, dwy = U.dev_params(wl.KAPPA, wx, wy)
+    r = shine.pipeline_fwd(img, k, dwx, dwy, "clamp")
+    sep = shine.pipeline_bwd(img, g, k, dwx, dwy, "clamp")
+    fused = shine.pipeline_fwd_bwd(img, g, k, dwx, dwy, "clamp")
+    torch.cuda.synchronize()
+    assert torch.equal(fused[0], r)
+    for x, y in zip(fused[1:], sep):
+        assert torch.equal(x, y)
