@@ -95,3 +95,20 @@ def test_precision_workload_fused_pass(shine, name):
     assert torch.equal(fused[0], r)
     for x, y in zip(fused[1:], sep):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("name", ["bf16", "f16"])
+def test_precision_workload_full_adjoint(shine, name):
+    """The adjoint of the full precision workload in the benchmark's launch configuration (the
+    eight-column kernel), every d img element against the oracle's reverse pass on the quantised
+    image and cotangent, and the parameter cotangents on the summation scale."""
+    dt = wl.storage_dtype(name)
+    img = wl.random_image(SIZE, SIZE, seed=0).to(dt)
+    g = wl.random_cotangent(SIZE, SIZE, seed=1).to(dt)
+    wx, wy = wl.sobel_weights()
+    k, dwx, dwy = U.dev_params(wl.KAPPA, wx, wy)
+    dgi, dgk, dgwx, dgwy = shine.pipeline_bwd(img.cuda(), g.cuda(), k, dwx, dwy, "clamp")
+    torch.cuda.synchronize()
+    ref = cref.backward(img, g, wl.KAPPA, wx, wy, "clamp", with_abs=True)
+    assert U.rel(U.host(dgi), ref[0]) <= U.TOL_16
+    U.assert_params((dgk, dgwx, dgwy), ref[1:])
