@@ -112,3 +112,20 @@ def test_precision_workload_full_adjoint(shine, name):
     ref = cref.backward(img, g, wl.KAPPA, wx, wy, "clamp", with_abs=True)
     assert U.rel(U.host(dgi), ref[0]) <= U.TOL_16
     U.assert_params((dgk, dgwx, dgwy), ref[1:])
+
+
+@pytest.mark.parametrize("name", ["bf16", "f16"])
+def test_precision_workload_full_forward(shine, name):
+    """The forward of the full precision workload, every element: R with float32 output from the
+    16-bit image against the oracle on the quantised input at the float32 tolerance, and R in
+    storage precision at the 16-bit one."""
+    dt = wl.storage_dtype(name)
+    img = wl.random_image(SIZE, SIZE, seed=0).to(dt)
+    wx, wy = wl.sobel_weights()
+    k, dwx, dwy = U.dev_params(wl.KAPPA, wx, wy)
+    r32 = shine.pipeline_fwd(img.cuda(), k, dwx, dwy, "clamp", out_dtype=torch.float32)
+    r16 = shine.pipeline_fwd(img.cuda(), k, dwx, dwy, "clamp")
+    torch.cuda.synchronize()
+    ref = cref.forward(img, wl.KAPPA, wx, wy, "clamp")
+    assert U.rel(U.host(r32), ref) <= U.TOL_F32
+    assert U.rel(U.host(r16), ref) <= U.TOL_16
